@@ -1,0 +1,221 @@
+"""Seeded synthetic inputs shared by the tests, the bench and the CPU oracle runs.
+
+This module only draws input keys and payloads.  It holds none of the sorting
+method's arithmetic (no sampling, no splitter choice, no classification), so the
+CUDA path and the CPU oracle can both consume its arrays without sharing code.
+
+Random numbers come from the counter-based form of SplitMix64 (Steele, Lea and
+Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014): the i-th
+output of the stream keyed ``k`` is ``mix(k + (i + 1) * GAMMA)``, which is exactly
+the (i+1)-th output of the sequential generator started from state ``k``.  A
+stream is keyed by ``mix(seed + (stream_id + 1) * GAMMA)``.  Everything is
+computed with wrapping int64 tensor arithmetic, so the same call gives the same
+bits on the CPU and on a CUDA device.
+
+The paper measures on random 32-byte strings (Section 3); its int32 / float64
+analogue here is the ``uniform`` distribution.  The other named distributions
+(Gaussian, all-zero, bucket-sorted, staggered, g-group, random duplicates) are
+not defined in the paper; their recipes below are this project's definitions
+and are documented with the design notes.
+"""
+from __future__ import annotations
+
+import torch
+
+MASK64 = (1 << 64) - 1
+GAMMA = 0x9E3779B97F4A7C15
+MIX1 = 0xBF58476D1CE4E5B9
+MIX2 = 0x94D049BB133111EB
+
+# Stream identifiers (the sampling stream of the random splitter choice is 1;
+# it is owned by the sorting code, not by this module).
+S_UNIFORM = 11
+S_GAUSS = 21            # 21..24: the four summed uniforms
+S_BUCKET = 31
+S_STAGGER = 41
+S_GGROUP = 51
+S_DUP_POOL = 61
+S_DUP_PICK = 62
+S_HOT_SEL = 71
+S_HOT_POOL = 72
+S_HOT_PICK = 73
+S_KEY64 = 74
+S_EDGE_KIND = 81
+S_EDGE_BITS = 82
+S_PAYLOAD = 91
+
+DISTRIBUTIONS = ("uniform", "gaussian", "zero", "bucket", "staggered", "ggroup", "dup")
+
+
+def _s64(x: int) -> int:
+    """Python int -> the int64 with the same low 64 bits."""
+    x &= MASK64
+    return x - (1 << 64) if x >= (1 << 63) else x
+
+
+def mix64_int(z: int) -> int:
+    """SplitMix64 output mix on a Python integer (reference form)."""
+    z &= MASK64
+    z = ((z ^ (z >> 30)) * MIX1) & MASK64
+    z = ((z ^ (z >> 27)) * MIX2) & MASK64
+    return z ^ (z >> 31)
+
+
+def stream_key(seed: int, stream: int) -> int:
+    return mix64_int((seed + (stream + 1) * GAMMA) & MASK64)
+
+
+def _lsr(z: torch.Tensor, k: int) -> torch.Tensor:
+    """Logical right shift of int64 bit patterns."""
+    return (z >> k) & ((1 << (64 - k)) - 1)
+
+
+def _mix_t(z: torch.Tensor) -> torch.Tensor:
+    z = z ^ _lsr(z, 30)
+    z = z * _s64(MIX1)
+    z = z ^ _lsr(z, 27)
+    z = z * _s64(MIX2)
+    return z ^ _lsr(z, 31)
+
+
+def u64(seed: int, stream: int, idx: torch.Tensor) -> torch.Tensor:
+    """Raw 64-bit outputs u(seed, stream, i) for int64 positions ``idx``.
+
+    Returned as int64 tensors holding the unsigned bit pattern."""
+    k = _s64(stream_key(seed, stream))
+    z = (idx + 1) * _s64(GAMMA) + k
+    return _mix_t(z)
+
+
+def _positions(n: int, start: int, count: int | None, device) -> torch.Tensor:
+    if count is None:
+        count = n - start
+    return torch.arange(start, start + count, dtype=torch.int64, device=device)
+
+
+def _v31(seed, stream, i):
+    """Uniform integers in [0, 2^31): the top 31 bits of u."""
+    return _lsr(u64(seed, stream, i), 33)
+
+
+def _unit(seed, stream, i):
+    """Uniform doubles in [0, 1): the top 53 bits of u times 2^-53 (exact)."""
+    return _lsr(u64(seed, stream, i), 11).to(torch.float64) * (2.0 ** -53)
+
+
+def int_keys(dist: str, n: int, seed: int, p: int, start: int = 0, count: int | None = None,
+             device="cpu") -> torch.Tensor:
+    """int64 keys in [0, 2^31) for the named distribution, positions [start, start+count)."""
+    i = _positions(n, start, count, device)
+    if n == 0 or i.numel() == 0:
+        return torch.zeros(0, dtype=torch.int64, device=device)
+    W = (1 << 31) // p
+    B = -(-n // p)                      # block length ceil(n/p)
+    if dist == "uniform":
+        return _v31(seed, S_UNIFORM, i)
+    if dist == "gaussian":
+        acc = torch.zeros_like(i)
+        for t in range(4):
+            acc = acc + _v31(seed, S_GAUSS + t, i)
+        return acc >> 2
+    if dist == "zero":
+        return torch.zeros_like(i)
+    if dist == "bucket":
+        # p contiguous blocks; inside each, sub-block j (of p) is uniform in [jW, (j+1)W).
+        o = i % B
+        j = (o * p) // B
+        return j * W + _v31(seed, S_BUCKET, i) % W
+    if dist == "staggered":
+        # block b is uniform in range index 2b+1 (b < p/2) or 2b-p (b >= p/2), width W.
+        b = i // B
+        half = p // 2
+        r = torch.where(b < half, 2 * b + 1, 2 * b - p)
+        r = r % p
+        return r * W + _v31(seed, S_STAGGER, i) % W
+    if dist == "ggroup":
+        # g = 8: block b of group G = b // 8 has 8 sub-blocks; sub-block j is uniform in
+        # range index (8G + p/2 + j) mod p, width W.
+        g = 8
+        b = i // B
+        G = b // g
+        o = i % B
+        j = (o * g) // B
+        r = (G * g + p // 2 + j) % p
+        return r * W + _v31(seed, S_GGROUP, i) % W
+    if dist == "dup":
+        pool = _v31(seed, S_DUP_POOL, torch.arange(32, dtype=torch.int64, device=device))
+        pick = _lsr(u64(seed, S_DUP_PICK, i), 1) % 32
+        return pool[pick]
+    raise ValueError(f"unknown distribution {dist!r}")
+
+
+def keys(dist: str, n: int, dtype: str, seed: int = 1, p: int = 1024, start: int = 0,
+         count: int | None = None, device="cpu") -> torch.Tensor:
+    """Keys of type ``dtype`` in {'i32', 'u64', 'f64'} for a named distribution.
+
+    i32: the integer recipe directly.  f64: uniform and Gaussian use 53-bit unit
+    doubles; the structured distributions use int_key * 2^-31 (exact).
+    u64: uniform 64-bit outputs for 'uniform', else the integer recipe widened."""
+    if dtype == "i32":
+        return int_keys(dist, n, seed, p, start, count, device).to(torch.int32)
+    if dtype == "f64":
+        i = _positions(n, start, count, device)
+        if dist == "uniform":
+            return _unit(seed, S_UNIFORM, i)
+        if dist == "gaussian":
+            acc = torch.zeros(i.shape, dtype=torch.float64, device=device)
+            for t in range(4):
+                acc = acc + _unit(seed, S_GAUSS + t, i)
+            return acc * 0.25
+        return int_keys(dist, n, seed, p, start, count, device).to(torch.float64) * (2.0 ** -31)
+    if dtype == "u64":
+        i = _positions(n, start, count, device)
+        if dist == "uniform":
+            return u64(seed, S_KEY64, i)
+        return int_keys(dist, n, seed, p, start, count, device)
+    raise ValueError(f"unknown dtype {dtype!r}")
+
+
+def hot_u64_keys(n: int, seed: int = 2, start: int = 0, count: int | None = None,
+                 device="cpu") -> torch.Tensor:
+    """u64 keys (int64 bit patterns): uniform 64-bit values, except that position i is
+    'hot' exactly when the top two bits of u(seed, HOT_SEL, i) are zero (probability
+    1/4) and then copies pool[floor(h * 1000 / 2^32)], h the top 32 bits of
+    u(seed, HOT_PICK, i), from a pool of 1000 values drawn from stream HOT_POOL."""
+    i = _positions(n, start, count, device)
+    if i.numel() == 0:
+        return torch.zeros(0, dtype=torch.int64, device=device)
+    pool = u64(seed, S_HOT_POOL, torch.arange(1000, dtype=torch.int64, device=device))
+    hot = _lsr(u64(seed, S_HOT_SEL, i), 62) == 0
+    pick = (_lsr(u64(seed, S_HOT_PICK, i), 32) * 1000) >> 32
+    cold = u64(seed, S_KEY64, i)
+    return torch.where(hot, pool[pick], cold)
+
+
+def edge_f64_keys(n: int, seed: int = 7, start: int = 0, count: int | None = None,
+                  device="cpu") -> torch.Tensor:
+    """float64 keys mixing +0, -0, +inf, -inf, signed subnormals and signed normals.
+
+    NaN is never produced (exponent 0x7FF only with a zero mantissa)."""
+    i = _positions(n, start, count, device)
+    if i.numel() == 0:
+        return torch.zeros(0, dtype=torch.float64, device=device)
+    kind = _lsr(u64(seed, S_EDGE_KIND, i), 61)          # 0..7
+    bits = u64(seed, S_EDGE_BITS, i)
+    sign = bits & _s64(1 << 63)
+    mant = bits & ((1 << 52) - 1)
+    exp = (_lsr(bits, 52) & 0x7FF) % 0x7FF              # 0..0x7FE: never inf/NaN
+    normal = sign | (exp << 52) | mant
+    sub = sign | torch.where(mant == 0, torch.ones_like(mant), mant)
+    out = normal
+    out = torch.where(kind == 0, torch.zeros_like(bits), out)                  # +0
+    out = torch.where(kind == 1, torch.full_like(bits, _s64(1 << 63)), out)    # -0
+    out = torch.where(kind == 2, torch.full_like(bits, 0x7FF << 52), out)      # +inf
+    out = torch.where(kind == 3, torch.full_like(bits, _s64((0xFFF) << 52)), out)  # -inf
+    out = torch.where(kind == 4, sub, out)                                     # subnormal
+    return out.view(torch.float64)
+
+
+def payload_index(n: int, start: int = 0, count: int | None = None, device="cpu") -> torch.Tensor:
+    """The u32 payload 'original index' (held in an int32 tensor)."""
+    return _positions(n, start, count, device).to(torch.int32)
