@@ -1,0 +1,321 @@
+// The C ABI of include/ossort.h: argument checks, workspace planning, dispatch
+// on the key type, statistics and the host-buffer variant.
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ossort.h"
+#include "driver.cuh"
+
+using namespace ossort;
+
+// ---- launch accounting and per-kernel event profiling ------------------------
+namespace {
+struct ProfRec {
+    const char* name;
+    cudaEvent_t a, b;
+};
+std::atomic<uint64_t> g_launches{0};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_recs;
+std::vector<cudaEvent_t> g_pool;
+thread_local const char* g_pending_name = nullptr;
+thread_local cudaEvent_t g_pending_a = nullptr;
+
+cudaEvent_t pool_event() {
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+}  // namespace
+
+namespace ossort {
+void prof_before(cudaStream_t st, const char* name) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on) return;
+    g_pending_name = name;
+    g_pending_a = pool_event();
+    cudaEventRecord(g_pending_a, st);
+}
+void prof_after(cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on || !g_pending_a) return;
+    cudaEvent_t b = pool_event();
+    cudaEventRecord(b, st);
+    g_recs.push_back(ProfRec{g_pending_name, g_pending_a, b});
+    g_pending_a = nullptr;
+}
+}  // namespace ossort
+
+namespace {
+
+thread_local int g_last_cuda = 0;
+
+int cuda_fail(cudaError_t e) {
+    g_last_cuda = (int)e;
+    return OS_ERR_CUDA;
+}
+
+size_t key_bytes(int kt) { return kt == OS_I32 ? 4 : 8; }
+
+int check_params(int kt, uint64_t n, const os_params* prm) {
+    if (kt < OS_I32 || kt > OS_F64 || !prm) return OS_ERR_ARG;
+    if (prm->split != OS_DET && prm->split != OS_RAN) return OS_ERR_ARG;
+    if (prm->p < 1 || prm->s < 1) return OS_ERR_ARG;
+    if (prm->flags & ~OS_STABLE) return OS_ERR_ARG;
+    if (n > OS_MAX_N || prm->p > OS_MAX_P || (uint64_t)prm->p * prm->s > OS_MAX_PS)
+        return OS_ERR_UNSUPPORTED;
+    return OS_OK;
+}
+
+int dispatch(int kt, RunArgs& a) {
+    switch (kt) {
+        case OS_I32: return run_i32(a);
+        case OS_U64: return run_u64(a);
+        default: return run_f64(a);
+    }
+}
+
+int num_sms_of_current_device() {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaGetLastError();
+    return sms > 0 ? sms : 152;
+}
+
+size_t plan_bytes(int kt, uint64_t n, bool has_vals, const os_params* prm) {
+    RunArgs a{};
+    a.n = n;
+    a.has_vals = has_vals;
+    a.prm = *prm;
+    a.ws = nullptr;
+    dispatch(kt, a);
+    return a.used + 256;
+}
+
+template <class KT>
+void splitters_to_host(const std::vector<typename KT::O>& o, void* dst) {
+    auto* d = static_cast<typename KT::T*>(dst);
+    for (size_t i = 0; i < o.size(); ++i) d[i] = KT::key(o[i]);
+}
+
+int fill_stats(int kt, const RunArgs& a, cudaStream_t st, os_stats* stats) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    uint32_t status[8];
+    e = cudaMemcpy(status, a.status, sizeof status, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const uint32_t p = a.prm.p, pu = a.res.p_used;
+    stats->p_used = pu;
+    stats->depth = status[1];
+    stats->repart_keys = (uint64_t)status[4] | ((uint64_t)status[5] << 32);
+    if (pu == 1) {
+        stats->max_bucket = a.n;
+        if (stats->bucket_sizes) {
+            for (uint32_t j = 0; j < p; ++j) stats->bucket_sizes[j] = 0;
+            stats->bucket_sizes[0] = a.n;
+        }
+    } else {
+        stats->max_bucket = status[2];
+        if (stats->bucket_sizes) {
+            std::vector<uint32_t> b(p);
+            e = cudaMemcpy(b.data(), a.res.bsize, p * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(e);
+            for (uint32_t j = 0; j < p; ++j) stats->bucket_sizes[j] = b[j];
+        }
+        if (stats->splitter_tags) {
+            std::vector<uint32_t> t(p - 1);
+            e = cudaMemcpy(t.data(), a.res.spl_t, (p - 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(e);
+            for (uint32_t j = 0; j + 1 < p; ++j) stats->splitter_tags[j] = t[j];
+        }
+        if (stats->splitter_keys) {
+            if (kt == OS_I32) {
+                std::vector<uint32_t> o(p - 1);
+                e = cudaMemcpy(o.data(), a.res.spl_o, (p - 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+                if (e != cudaSuccess) return cuda_fail(e);
+                splitters_to_host<KeyI32>(o, stats->splitter_keys);
+            } else {
+                std::vector<uint64_t> o(p - 1);
+                e = cudaMemcpy(o.data(), a.res.spl_o, (p - 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+                if (e != cudaSuccess) return cuda_fail(e);
+                if (kt == OS_U64) splitters_to_host<KeyU64>(o, stats->splitter_keys);
+                else splitters_to_host<KeyF64>(o, stats->splitter_keys);
+            }
+        }
+    }
+    return status[0] ? OS_ERR_DEVICE : OS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t os_launch_count(void) { return g_launches.load(); }
+
+int os_profile_start(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto& r : g_recs) {
+        g_pool.push_back(r.a);
+        g_pool.push_back(r.b);
+    }
+    g_recs.clear();
+    g_prof_on = true;
+    return OS_OK;
+}
+
+int os_profile_stop(os_kernel_time* out, int max_entries, int* n_entries) {
+    std::vector<ProfRec> recs;
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        g_prof_on = false;
+        recs.swap(g_recs);
+    }
+    std::vector<os_kernel_time> agg;
+    int rc = OS_OK;
+    for (auto& r : recs) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) rc = cuda_fail(e);
+        size_t i = 0;
+        while (i < agg.size() && std::strncmp(agg[i].name, r.name, sizeof(agg[i].name)) != 0) ++i;
+        if (i == agg.size()) {
+            os_kernel_time t{};
+            std::strncpy(t.name, r.name, sizeof(t.name) - 1);
+            agg.push_back(t);
+        }
+        agg[i].launches += 1;
+        agg[i].total_ms += ms;
+        if (ms > agg[i].max_ms) agg[i].max_ms = ms;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        for (auto& r : recs) {
+            g_pool.push_back(r.a);
+            g_pool.push_back(r.b);
+        }
+    }
+    if (n_entries) *n_entries = (int)agg.size();
+    if (out)
+        for (int i = 0; i < (int)agg.size() && i < max_entries; ++i) out[i] = agg[i];
+    return rc;
+}
+
+int os_version(void) { return OSSORT_VERSION; }
+
+int os_last_cuda_error(void) { return g_last_cuda; }
+
+const char* os_strerror(int status) {
+    switch (status) {
+        case OS_OK: return "ok";
+        case OS_ERR_ARG: return "invalid argument";
+        case OS_ERR_WS: return "workspace missing or too small";
+        case OS_ERR_UNSUPPORTED: return "size or parameter beyond the supported limits";
+        case OS_ERR_CUDA: return "CUDA call failed";
+        case OS_ERR_DEVICE: return "a kernel reported an internal error";
+        default: return "unknown status";
+    }
+}
+
+int os_workspace_size(int key_type, uint64_t n, int has_vals, const os_params* prm, size_t* bytes) {
+    if (!bytes) return OS_ERR_ARG;
+    int rc = check_params(key_type, n, prm);
+    if (rc) return rc;
+    *bytes = plan_bytes(key_type, n, has_vals != 0, prm);
+    return OS_OK;
+}
+
+int os_sort(int key_type, const void* d_keys_in, void* d_keys_out, const uint32_t* d_vals_in, uint32_t* d_vals_out,
+            uint64_t n, const os_params* prm, void* d_ws, size_t ws_bytes, void* stream, os_stats* stats) {
+    int rc = check_params(key_type, n, prm);
+    if (rc) return rc;
+    if (n > 0 && (!d_keys_in || !d_keys_out)) return OS_ERR_ARG;
+    if ((d_vals_in != nullptr) != (d_vals_out != nullptr)) return OS_ERR_ARG;
+    const bool hv = d_vals_in != nullptr;
+    const size_t need = plan_bytes(key_type, n, hv, prm);
+    if (!d_ws || ws_bytes < need) return OS_ERR_WS;
+    RunArgs a{};
+    a.kin = d_keys_in;
+    a.kout = d_keys_out;
+    a.vin = d_vals_in;
+    a.vout = d_vals_out;
+    a.has_vals = hv;
+    a.n = n;
+    a.prm = *prm;
+    a.ws = d_ws;
+    a.ws_bytes = ws_bytes;
+    a.st = static_cast<cudaStream_t>(stream);
+    a.num_sms = num_sms_of_current_device();
+    dispatch(key_type, a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (stats) return fill_stats(key_type, a, a.st, stats);
+    return OS_OK;
+}
+
+int os_workspace_size_host(int key_type, uint64_t n, int has_vals, const os_params* prm, size_t* bytes) {
+    size_t inner = 0;
+    int rc = os_workspace_size(key_type, n, has_vals, prm, &inner);
+    if (rc) return rc;
+    const size_t kb = ((n * key_bytes(key_type)) + 255) & ~size_t(255);
+    const size_t vb = has_vals ? ((n * 4 + 255) & ~size_t(255)) : 0;
+    *bytes = ((inner + 255) & ~size_t(255)) + kb + vb;
+    return OS_OK;
+}
+
+int os_sort_host(int key_type, const void* h_keys_in, void* h_keys_out, const uint32_t* h_vals_in,
+                 uint32_t* h_vals_out, uint64_t n, const os_params* prm, void* d_ws, size_t ws_bytes,
+                 void* stream) {
+    int rc = check_params(key_type, n, prm);
+    if (rc) return rc;
+    if (n > 0 && (!h_keys_in || !h_keys_out)) return OS_ERR_ARG;
+    if ((h_vals_in != nullptr) != (h_vals_out != nullptr)) return OS_ERR_ARG;
+    const bool hv = h_vals_in != nullptr;
+    size_t need = 0;
+    os_workspace_size_host(key_type, n, hv, prm, &need);
+    if (!d_ws || ws_bytes < need) return OS_ERR_WS;
+    const size_t inner = (plan_bytes(key_type, n, hv, prm) + 255) & ~size_t(255);
+    char* base = static_cast<char*>(d_ws);
+    void* dk = base + inner;
+    uint32_t* dv = hv ? reinterpret_cast<uint32_t*>(base + inner + (((n * key_bytes(key_type)) + 255) & ~size_t(255)))
+                      : nullptr;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t kbytes = n * key_bytes(key_type);
+    cudaError_t e = cudaSuccess;
+    if (n > 0) {
+        e = cudaMemcpyAsync(dk, h_keys_in, kbytes, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && hv) e = cudaMemcpyAsync(dv, h_vals_in, n * 4, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    rc = os_sort(key_type, dk, dk, dv, dv, n, prm, d_ws, inner, stream, nullptr);
+    if (rc) return rc;
+    if (n > 0) {
+        e = cudaMemcpyAsync(h_keys_out, dk, kbytes, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && hv) e = cudaMemcpyAsync(h_vals_out, dv, n * 4, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return os_check(d_ws, stream, nullptr);
+}
+
+int os_check(const void* d_ws, void* stream, uint32_t* bits) {
+    if (!d_ws) return OS_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e);
+    uint32_t word = 0;
+    e = cudaMemcpy(&word, d_ws, sizeof word, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (bits) *bits = word;
+    return word ? OS_ERR_DEVICE : OS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// Shared device definitions of the GB300 sample sort: key traits, tagged keys,
+// the counter-based SplitMix64, launch constants and the workspace arena.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ossort {
+
+// ---------------------------------------------------------------------------
+// Key traits.  Every kernel works on an unsigned "ordered" image of the key
+// whose unsigned order is the key order, and converts back on store.
+//   int32  : flip the sign bit.
+//   uint64 : identity.
+//   float64: IEEE 754 totalOrder map -- negative numbers have every bit
+//            inverted, non-negative ones get the sign bit set.
+//   uint32 : identity (internal: sorting sample positions).
+// ---------------------------------------------------------------------------
+struct KeyI32 {
+    using T = int32_t;
+    using O = uint32_t;
+    static __host__ __device__ __forceinline__ O ord(T x) { return (uint32_t)x ^ 0x80000000u; }
+    static __host__ __device__ __forceinline__ T key(O o) { return (int32_t)(o ^ 0x80000000u); }
+};
+struct KeyU32 {
+    using T = uint32_t;
+    using O = uint32_t;
+    static __host__ __device__ __forceinline__ O ord(T x) { return x; }
+    static __host__ __device__ __forceinline__ T key(O o) { return o; }
+};
+struct KeyU64 {
+    using T = uint64_t;
+    using O = uint64_t;
+    static __host__ __device__ __forceinline__ O ord(T x) { return x; }
+    static __host__ __device__ __forceinline__ T key(O o) { return o; }
+};
+struct KeyF64 {  // T holds the raw bits of the double
+    using T = uint64_t;
+    using O = uint64_t;
+    static __host__ __device__ __forceinline__ O ord(T b) {
+        return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+    }
+    static __host__ __device__ __forceinline__ T key(O o) {
+        return (o >> 63) ? (o & 0x7FFFFFFFFFFFFFFFull) : ~o;
+    }
+};
+
+template <class O> struct OMax;
+template <> struct OMax<uint32_t> { static constexpr uint32_t v = 0xFFFFFFFFu; };
+template <> struct OMax<uint64_t> { static constexpr uint64_t v = 0xFFFFFFFFFFFFFFFFull; };
+
+// ---------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014), counter form: output i of
+// the generator whose state starts at `state` is mix(state + (i + 1) GAMMA);
+// stream `st` of `seed` starts at mix(seed + (st + 1) GAMMA).
+// ---------------------------------------------------------------------------
+constexpr uint64_t SM_GAMMA = 0x9E3779B97F4A7C15ull;
+
+__host__ __device__ __forceinline__ uint64_t sm_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t sm_stream(uint64_t seed, uint64_t st) {
+    return sm_mix(seed + (st + 1) * SM_GAMMA);
+}
+__host__ __device__ __forceinline__ uint64_t sm_at(uint64_t state, uint64_t i) {
+    return sm_mix(state + (i + 1) * SM_GAMMA);
+}
+
+// ---------------------------------------------------------------------------
+// Launch constants.
+// ---------------------------------------------------------------------------
+constexpr int MAX_P = 4096;          // largest p (bucket ids fit 16 bits)
+constexpr int TOP_NT = 256;          // threads of the grid-wide classify / scatter
+constexpr int TOP_IT = 16;           // keys per thread per tile
+constexpr int TOP_TILE = TOP_NT * TOP_IT;
+constexpr int TOP_WARPS = TOP_NT / 32;
+
+constexpr int BK_NT = 512;           // threads of the bucket kernel
+constexpr int BK_WARPS = BK_NT / 32;
+constexpr int MAXP2 = 256;           // largest fan-out of an in-bucket repartition
+constexpr int MAX_DEPTH = 4;         // repartition levels below a segment
+constexpr int SAMPLE2 = 4096;        // sample size of an in-bucket repartition
+
+// keys per thread of the shared-memory bucket sort: 16 for 4-byte keys, 8 for 8-byte keys
+template <class O> struct LeafIT { static constexpr int v = sizeof(O) == 4 ? 16 : 8; };
+template <class O> struct Cap { static constexpr int v = BK_NT * LeafIT<O>::v; };
+
+// Error bits of the device status word.
+constexpr uint32_t ERR_DEPTH = 1u;         // a bucket still too large at MAX_DEPTH
+constexpr uint32_t ERR_SIZES = 2u;         // a work list overflowed
+constexpr uint32_t ERR_SAMPLE = 4u;        // sample larger than its buffer
+
+// ---------------------------------------------------------------------------
+// Workspace arena: a bump allocator over the caller's workspace.  In measure
+// mode (base == nullptr) it only adds up sizes, so os_workspace_size runs the
+// same planning code as os_sort.
+// ---------------------------------------------------------------------------
+struct Arena {
+    char* base = nullptr;
+    size_t cap = 0;
+    size_t used = 0;
+    bool measure() const { return base == nullptr; }
+    template <class X> X* take(size_t count) {
+        size_t off = (used + 255) & ~size_t(255);
+        used = off + count * sizeof(X);
+        if (measure() || used > cap) return nullptr;
+        return reinterpret_cast<X*>(base + off);
+    }
+};
+
+}  // namespace ossort

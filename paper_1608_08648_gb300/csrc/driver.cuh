@@ -1,0 +1,326 @@
+// Host-side orchestration of one sort: plans the workspace, launches the
+// kernels of kernels.cuh on the caller's stream, never synchronizes.
+//
+// SqRan (Algorithm 2, with the sample on original positions):
+//   sample p s - 1 positions, sort them, gather the tagged keys, sort the sample,
+//   pick p - 1 splitters, classify + scatter every key into its bucket, sort
+//   every bucket.
+// SqDet (Algorithm 1):
+//   sort the p sequences (step 1), take r p regular samples from each (step 2),
+//   sort the r p^2 samples and pick the splitters (step 3), classify + scatter
+//   the sorted sequences into buckets (step 4), sort every bucket (step 5).
+#pragma once
+
+#include <algorithm>
+
+#include "../../include/ossort.h"
+#include "kernels.cuh"
+#include "profile.cuh"
+
+namespace ossort {
+
+struct Ctx {
+    cudaStream_t st = nullptr;
+    Arena ar;
+    int num_sms = 152;
+    uint32_t* status = nullptr;   // [0] error bits, [1] depth, [2] max bucket, [4..5] u64 repartitioned keys
+    bool nested = false;          // inside the sort of a sample (launch names get a ".sample" suffix)
+    bool live() const { return !ar.measure(); }
+};
+
+inline uint32_t pow2_ceil(uint32_t x) {
+    uint32_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+inline int log2_exact(uint32_t x) {
+    int h = 0;
+    while ((1u << h) < x) ++h;
+    return h;
+}
+inline unsigned grid_for(uint64_t work, int threads, unsigned cap = 4096) {
+    uint64_t g = (work + threads - 1) / threads;
+    return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(g, cap));
+}
+
+constexpr uint32_t G_CAP = 2048;   // most CTAs of the grid-wide classify / scatter
+
+template <class K>
+int occupancy(K kernel, int threads, size_t smem) {
+    int occ = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem);
+    return occ > 0 ? occ : 1;
+}
+
+// Sort every segment of ss (stably, in the tagged order of positions inside
+// the segment).  Level-0 data is in src (read only); other and alt are scratch
+// buffers of the same length (alt may be src when src is writable); the sorted
+// segments land in out (which may be other).
+template <class KT, bool HV>
+void segment_sort(Ctx& c, SegSpec ss, const typename KT::T* src, const uint32_t* vsrc, typename KT::T* other,
+                  uint32_t* vother, typename KT::T* alt, uint32_t* valt, typename KT::T* out, uint32_t* vout,
+                  uint64_t seed) {
+    using O = typename KT::O;
+    using L = BucketSmem<KT, HV>;
+    constexpr uint64_t CAP = (uint64_t)L::CAP;
+    if (ss.nseg == 0 || ss.n == 0) return;
+    SortBufs<KT> bufs;
+    bufs.k[0] = const_cast<typename KT::T*>(src);
+    bufs.v[0] = const_cast<uint32_t*>(vsrc);
+    bufs.k[1] = other;
+    bufs.v[1] = vother;
+    bufs.k[2] = alt;
+    bufs.v[2] = valt;
+    bufs.out = out;
+    bufs.vout = vout;
+    WorkLists wl{};
+    const bool direct = ss.off == nullptr && (ss.n + ss.nseg - 1) / ss.nseg <= CAP;
+    if (!direct) {
+        wl.counts = c.ar.take<uint32_t>(MAX_DEPTH + 1);
+        wl.part_cap = (uint32_t)(ss.n / CAP + 1);
+        wl.leaf_cap = (uint32_t)(ss.nseg + (uint64_t)MAX_DEPTH * 6 * wl.part_cap);
+        wl.leaf = c.ar.take<WorkItem>(wl.leaf_cap);
+        wl.part[0] = c.ar.take<WorkItem>(wl.part_cap);
+        wl.part[1] = c.ar.take<WorkItem>(wl.part_cap);
+    }
+    if (!c.live()) return;
+    cudaFuncSetAttribute(k_leaf<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::leaf_bytes);
+    const uint32_t grid_l = (uint32_t)(c.num_sms * occupancy(k_leaf<KT, HV>, BK_NT, L::leaf_bytes));
+    if (direct) {
+        OS_LAUNCH(c.st, c.nested ? "k_leaf.sample" : "k_leaf",
+                  k_leaf<KT, HV><<<std::min(ss.nseg, grid_l), BK_NT, L::leaf_bytes, c.st>>>(true, ss, bufs, wl));
+        return;
+    }
+    cudaMemsetAsync(wl.counts, 0, sizeof(uint32_t) * (MAX_DEPTH + 1), c.st);
+    cudaFuncSetAttribute(k_repart<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+    const uint32_t grid_r = (uint32_t)(c.num_sms * occupancy(k_repart<KT, HV>, BK_NT, L::bytes));
+    for (int level = 0; level < MAX_DEPTH; ++level) {
+        const uint32_t g = level == 0 ? std::min(ss.nseg, grid_r) : grid_r;
+        OS_LAUNCH(c.st, c.nested ? "k_repart.sample" : "k_repart",
+                  k_repart<KT, HV><<<g, BK_NT, L::bytes, c.st>>>(level, ss, bufs, wl, seed, c.status, c.status + 1,
+                                                                 reinterpret_cast<unsigned long long*>(c.status + 4)));
+    }
+    OS_LAUNCH(c.st, c.nested ? "k_leaf.sample" : "k_leaf", k_leaf<KT, HV><<<grid_l, BK_NT, L::leaf_bytes, c.st>>>(false, ss, bufs, wl));
+}
+
+template <class KT>
+size_t classify_smem(int p, int P) {
+    return (size_t)Tree<typename KT::O>::node_bytes * P + sizeof(uint32_t) * p;
+}
+
+template <class KT, bool HV>
+size_t scatter_smem(int p, int P) {
+    using T = typename KT::T;
+    size_t b = ((size_t)Tree<typename KT::O>::node_bytes * P + 15) & ~size_t(15);
+    b += sizeof(T) * TOP_TILE + (HV ? sizeof(uint32_t) * TOP_TILE : 0);
+    b += sizeof(uint32_t) * (p + 1) + sizeof(uint32_t) * p + sizeof(uint32_t) * 32;
+    b += sizeof(uint16_t) * TOP_TILE + sizeof(uint16_t) * TOP_WARPS * (p + 1);
+    return b;
+}
+
+// Step 4: classify every key of src (tag = position) against the p-1 sorted
+// splitters and scatter keys (and payloads) into contiguous buckets of dst.
+// Bucket b occupies [boff[b], boff[b+1]); bsize[b] = its size.
+template <class KT, bool HV>
+void partition_top(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, uint32_t n,
+                   const typename KT::O* spl_o, const uint32_t* spl_t, uint32_t p, typename KT::T* dst,
+                   uint32_t* vdst, uint32_t* boff, uint32_t* bsize) {
+    const uint32_t P = pow2_ceil(p);
+    const int h = log2_exact(P);
+    const uint32_t ntiles = (n + TOP_TILE - 1) / TOP_TILE;
+    const uint32_t gmax = std::min<uint32_t>(std::max<uint32_t>(ntiles, 1), G_CAP);
+    uint32_t* hist = c.ar.take<uint32_t>((size_t)p * gmax);
+    uint32_t* col = c.ar.take<uint32_t>((size_t)p * gmax);
+    if (!c.live()) return;
+    const size_t sm_c = classify_smem<KT>(p, P), sm_s = scatter_smem<KT, HV>(p, P);
+    cudaFuncSetAttribute(k_classify<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c);
+    cudaFuncSetAttribute(k_scatter<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_s);
+    const int occ = occupancy(k_scatter<KT, HV>, TOP_NT, sm_s);
+    const uint32_t G = std::max<uint32_t>(1, std::min<uint32_t>(gmax, (uint32_t)(c.num_sms * occ)));
+    OS_LAUNCH(c.st, c.nested ? "k_classify.sample" : "k_classify",
+              k_classify<KT><<<G, TOP_NT, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, h, hist, ntiles));
+    OS_LAUNCH(c.st, c.nested ? "k_column_scan.sample" : "k_column_scan",
+              k_column_scan<<<grid_for((uint64_t)p * 32, 256), 256, 0, c.st>>>(hist, p, G, col, bsize));
+    OS_LAUNCH(c.st, c.nested ? "k_bucket_offsets.sample" : "k_bucket_offsets", k_bucket_offsets<<<1, 1024, 0, c.st>>>(bsize, p, boff, c.status + 2));
+    OS_LAUNCH(c.st, c.nested ? "k_scatter.sample" : "k_scatter",
+              k_scatter<KT, HV><<<G, TOP_NT, sm_s, c.st>>>(src, vsrc, n, spl_o, spl_t, (int)p, h, col, boff, dst,
+                                                           vdst, ntiles));
+}
+
+template <class KT, bool HV>
+void sort_array(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, typename KT::T* out, uint32_t* vout,
+                uint32_t n, uint64_t seed);
+
+// Step 2 (SqRan) and step 3: p s - 1 tagged random keys, sorted; splitters at
+// ranks i s - 1.
+template <class KT>
+void splitters_ran(Ctx& c, const typename KT::T* keys, uint32_t n, uint32_t p, uint32_t s, uint64_t seed,
+                   typename KT::O* spl_o, uint32_t* spl_t) {
+    using T = typename KT::T;
+    const uint32_t m = p * s - 1;
+    uint32_t* pos = c.ar.take<uint32_t>(m);
+    uint32_t* pos_s = c.ar.take<uint32_t>(m);
+    T* tk = c.ar.take<T>(m);
+    uint32_t* tt = c.ar.take<uint32_t>(m);
+    T* tks = c.ar.take<T>(m);
+    uint32_t* tts = c.ar.take<uint32_t>(m);
+    if (c.live())
+        OS_LAUNCH(c.st, "k_ran_positions",
+                  k_ran_positions<<<grid_for(m, 256, 1024), 256, 0, c.st>>>(pos, m, n, seed));
+    // Positions in increasing order, so that a stable sort by key leaves equal
+    // keys in tag order.
+    const bool was_nested = c.nested;
+    c.nested = true;
+    sort_array<KeyU32, false>(c, pos, nullptr, pos_s, nullptr, m, sm_mix(seed ^ 0x51ull));
+    if (c.live())
+        OS_LAUNCH(c.st, "k_gather_tagged",
+                  k_gather_tagged<KT><<<grid_for(m, 256, 1024), 256, 0, c.st>>>(keys, pos_s, m, tk, tt));
+    sort_array<KT, true>(c, tk, tt, tks, tts, m, sm_mix(seed ^ 0x52ull));
+    c.nested = was_nested;
+    if (c.live() && p > 1)
+        OS_LAUNCH(c.st, "k_pick_splitters",
+                  k_pick_splitters<KT><<<grid_for(p, 256), 256, 0, c.st>>>(tks, tts, p, s, spl_o, spl_t));
+}
+
+// Steps 2-3 of SqDet: r p regular samples from each sorted sequence of A
+// (already in tag order), sorted stably by key; splitters at ranks i r p - 1.
+template <class KT>
+void splitters_det(Ctx& c, const typename KT::T* A, uint32_t n, uint32_t p, uint32_t r, uint64_t seed,
+                   typename KT::O* spl_o, uint32_t* spl_t) {
+    using T = typename KT::T;
+    const uint32_t mm = r * p;
+    const uint64_t m = (uint64_t)p * mm;
+    T* tk = c.ar.take<T>(m);
+    uint32_t* tt = c.ar.take<uint32_t>(m);
+    T* tks = c.ar.take<T>(m);
+    uint32_t* tts = c.ar.take<uint32_t>(m);
+    if (c.live())
+        OS_LAUNCH(c.st, "k_det_sample", k_det_sample<KT><<<grid_for(m, 256), 256, 0, c.st>>>(A, n, p, mm, tk, tt));
+    const bool was_nested = c.nested;
+    c.nested = true;
+    sort_array<KT, true>(c, tk, tt, tks, tts, (uint32_t)m, sm_mix(seed ^ 0x53ull));
+    c.nested = was_nested;
+    if (c.live() && p > 1)
+        OS_LAUNCH(c.st, "k_pick_splitters",
+                  k_pick_splitters<KT><<<grid_for(p, 256), 256, 0, c.st>>>(tks, tts, p, mm, spl_o, spl_t));
+}
+
+// Sort any array (used for samples and for inputs too small to sample): one
+// shared-memory sort when it fits a CTA, else an internal SqRan level with p
+// chosen so that buckets are a few CTA capacities.
+template <class KT, bool HV>
+void sort_array(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, typename KT::T* out, uint32_t* vout,
+                uint32_t n, uint64_t seed) {
+    using T = typename KT::T;
+    using O = typename KT::O;
+    constexpr uint32_t CAP = (uint32_t)Cap<O>::v;
+    if (n == 0) return;
+    if (n <= CAP) {
+        segment_sort<KT, HV>(c, SegSpec{nullptr, 1, n}, src, vsrc, nullptr, nullptr, nullptr, nullptr, out, vout,
+                             seed);
+        return;
+    }
+    const uint32_t p = std::min<uint32_t>(1024, std::max<uint32_t>(2, pow2_ceil(n / (2 * CAP))));
+    const uint32_t s = std::max<uint32_t>(1, CAP / p);
+    O* spl_o = c.ar.take<O>(p - 1);
+    uint32_t* spl_t = c.ar.take<uint32_t>(p - 1);
+    uint32_t* boff = c.ar.take<uint32_t>(p + 1);
+    uint32_t* bsize = c.ar.take<uint32_t>(p);
+    T* w = c.ar.take<T>(n);
+    uint32_t* vw = HV ? c.ar.take<uint32_t>(n) : nullptr;
+    splitters_ran<KT>(c, src, n, p, s, seed, spl_o, spl_t);
+    partition_top<KT, HV>(c, src, vsrc, n, spl_o, spl_t, p, w, vw, boff, bsize);
+    segment_sort<KT, HV>(c, SegSpec{boff, p, n}, w, vw, out, vout, w, vw, out, vout, sm_mix(seed ^ 0x54ull));
+}
+
+// Device results of one user-level sort (for statistics).
+struct TopResult {
+    uint32_t p_used = 1;
+    void* spl_o = nullptr;
+    uint32_t* spl_t = nullptr;
+    uint32_t* bsize = nullptr;
+};
+
+template <class KT, bool HV>
+void sort_top(Ctx& c, const typename KT::T* kin, typename KT::T* kout, const uint32_t* vin, uint32_t* vout,
+              uint32_t n, const os_params& prm, TopResult& res) {
+    using T = typename KT::T;
+    using O = typename KT::O;
+    const uint32_t p = prm.p, s = prm.s;
+    const uint64_t ps = (uint64_t)p * s;
+    const uint64_t internal_seed = sm_mix(prm.seed ^ 0xA5A5A5A5A5A5A5A5ull);
+    const bool small = (p == 1) || (prm.split == OS_RAN ? ((uint64_t)n < 2 * ps)
+                                                        : (((uint64_t)n + p - 1) / p < ps));
+    O* spl_o = c.ar.take<O>(std::max<uint32_t>(p - 1, 1));
+    uint32_t* spl_t = c.ar.take<uint32_t>(std::max<uint32_t>(p - 1, 1));
+    uint32_t* boff = c.ar.take<uint32_t>(p + 1);
+    uint32_t* bsize = c.ar.take<uint32_t>(p);
+    res.spl_o = spl_o;
+    res.spl_t = spl_t;
+    res.bsize = bsize;
+    res.p_used = small ? 1 : p;
+    if (n == 0) return;
+    if (small) {
+        sort_array<KT, HV>(c, kin, vin, kout, vout, n, internal_seed);
+        return;
+    }
+    T* w1 = c.ar.take<T>(n);
+    uint32_t* vw1 = HV ? c.ar.take<uint32_t>(n) : nullptr;
+    if (prm.split == OS_RAN) {
+        splitters_ran<KT>(c, kin, n, p, s, prm.seed, spl_o, spl_t);
+        partition_top<KT, HV>(c, kin, vin, n, spl_o, spl_t, p, w1, vw1, boff, bsize);
+        segment_sort<KT, HV>(c, SegSpec{boff, p, n}, w1, vw1, kout, vout, w1, vw1, kout, vout, internal_seed);
+    } else {
+        T* w2 = c.ar.take<T>(n);
+        uint32_t* vw2 = HV ? c.ar.take<uint32_t>(n) : nullptr;
+        // Step 1: the p sequences sorted into w1 (stable).
+        segment_sort<KT, HV>(c, SegSpec{nullptr, p, n}, kin, vin, w2, vw2, w1, vw1, w1, vw1, internal_seed);
+        splitters_det<KT>(c, w1, n, p, s, internal_seed, spl_o, spl_t);
+        partition_top<KT, HV>(c, w1, vw1, n, spl_o, spl_t, p, w2, vw2, boff, bsize);
+        segment_sort<KT, HV>(c, SegSpec{boff, p, n}, w2, vw2, kout, vout, w2, vw2, kout, vout, internal_seed);
+    }
+}
+
+// Everything one os_sort call needs, independent of the key type.
+struct RunArgs {
+    const void* kin;
+    void* kout;
+    const uint32_t* vin;
+    uint32_t* vout;
+    bool has_vals;
+    uint64_t n;
+    os_params prm;
+    void* ws;          // nullptr: measure only
+    size_t ws_bytes;
+    cudaStream_t st;
+    int num_sms;
+    // outputs
+    size_t used;
+    uint32_t* status;
+    TopResult res;
+};
+
+template <class KT>
+int run_sort(RunArgs& a) {
+    using T = typename KT::T;
+    Ctx c;
+    c.st = a.st;
+    c.num_sms = a.num_sms;
+    c.ar.base = static_cast<char*>(a.ws);
+    c.ar.cap = a.ws_bytes;
+    c.status = c.ar.take<uint32_t>(8);
+    if (c.live()) cudaMemsetAsync(c.status, 0, 8 * sizeof(uint32_t), c.st);
+    const T* kin = static_cast<const T*>(a.kin);
+    T* kout = static_cast<T*>(a.kout);
+    if (a.has_vals) sort_top<KT, true>(c, kin, kout, a.vin, a.vout, (uint32_t)a.n, a.prm, a.res);
+    else sort_top<KT, false>(c, kin, kout, nullptr, nullptr, (uint32_t)a.n, a.prm, a.res);
+    a.used = c.ar.used;
+    a.status = c.status;
+    return 0;
+}
+
+int run_i32(RunArgs& a);
+int run_u64(RunArgs& a);
+int run_f64(RunArgs& a);
+
+}  // namespace ossort

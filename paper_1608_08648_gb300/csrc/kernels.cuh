@@ -1,0 +1,675 @@
+// Kernels of the GB300 oversampling sample sort.
+//
+// Paper step -> kernel:
+//   step 1 (SqDet BaselineSorting)      k_repart + k_leaf over p uniform sequences
+//   step 2 (SqDet regular sample)       k_det_sample
+//   step 2 (SqRan random sample)        k_ran_positions + k_gather_tagged
+//   steps 2-3 (sample sort, splitters)  k_leaf (or a nested sort) + k_pick_splitters
+//   step 4 (split)                      k_classify + k_column_scan + k_bucket_offsets
+//                                       + k_scatter (keys land in contiguous buckets)
+//   step 5 (sort every bucket)          k_repart + k_leaf over the p buckets
+#pragma once
+
+#include "blocksort.cuh"
+#include "common.cuh"
+
+namespace ossort {
+
+// ---------------------------------------------------------------------------
+// Splitter search tree in shared memory: the p-1 tagged splitters (padded with
+// +inf up to P-1, P a power of two) in breadth-first (Eytzinger) order, so the
+// bucket of a key is found with log2(P) branch-free steps.
+// The bucket of x is the number of splitters strictly below x in the tagged
+// order (Section 2.2), so a key equal to a splitter closes the lower bucket.
+// ---------------------------------------------------------------------------
+template <class O> struct Tree;
+
+template <> struct Tree<uint32_t> {
+    uint64_t* c;
+    static constexpr int node_bytes = 8;
+    __device__ __forceinline__ void bind(char* p, int) { c = reinterpret_cast<uint64_t*>(p); }
+    __device__ __forceinline__ void set(int v, uint32_t o, uint32_t t) { c[v] = ((uint64_t)o << 32) | t; }
+    __device__ __forceinline__ void set_inf(int v) { c[v] = ~0ull; }
+    __device__ __forceinline__ int find(uint32_t o, uint32_t t, int h) const {
+        const uint64_t x = ((uint64_t)o << 32) | t;
+        int v = 1;
+        for (int d = 0; d < h; ++d) v = 2 * v + (x > c[v] ? 1 : 0);
+        return v - (1 << h);
+    }
+};
+
+template <> struct Tree<uint64_t> {
+    uint64_t* o_;
+    uint32_t* t_;
+    static constexpr int node_bytes = 12;
+    __device__ __forceinline__ void bind(char* p, int P) {
+        o_ = reinterpret_cast<uint64_t*>(p);
+        t_ = reinterpret_cast<uint32_t*>(p + sizeof(uint64_t) * P);
+    }
+    __device__ __forceinline__ void set(int v, uint64_t o, uint32_t t) { o_[v] = o; t_[v] = t; }
+    __device__ __forceinline__ void set_inf(int v) { o_[v] = ~0ull; t_[v] = ~0u; }
+    __device__ __forceinline__ int find(uint64_t o, uint32_t t, int h) const {
+        int v = 1;
+        for (int d = 0; d < h; ++d) {
+            const uint64_t so = o_[v];
+            v = 2 * v + (((o > so) | ((o == so) & (t > t_[v]))) ? 1 : 0);
+        }
+        return v - (1 << h);
+    }
+};
+
+// In-order rank (1-based) of Eytzinger node v in a complete tree of height h.
+__device__ __forceinline__ int eytz_rank(int v, int h) {
+    const int d = 31 - __clz(v);
+    return (2 * (v - (1 << d)) + 1) << (h - 1 - d);
+}
+
+// Fill the tree from sorted splitter arrays spl_o / spl_t of length p-1.
+template <class O>
+__device__ void tree_from_arrays(Tree<O>& tr, const O* spl_o, const uint32_t* spl_t, int p, int h) {
+    const int P = 1 << h;
+    for (int v = threadIdx.x + 1; v < P; v += blockDim.x) {
+        const int i = eytz_rank(v, h);
+        if (i < p) tr.set(v, spl_o[i - 1], spl_t[i - 1]);
+        else tr.set_inf(v);
+    }
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// In-place exclusive scan of a[0, len) in shared memory by the whole block;
+// returns the total.  scratch: 32 words.  Starts and ends with __syncthreads.
+static __device__ uint32_t block_exclusive_scan(uint32_t* a, int len, uint32_t* scratch) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int per = (len + nt - 1) / nt;
+    const int lo = min(len, tid * per), hi = min(len, lo + per);
+    __syncthreads();
+    uint32_t sum = 0;
+    for (int i = lo; i < hi; ++i) sum += a[i];
+    const int lane = tid & 31, w = tid >> 5;
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) scratch[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        const int nw = nt >> 5;
+        uint32_t z = lane < nw ? scratch[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o) z += y;
+        }
+        if (lane < nw) scratch[lane] = z;   // inclusive warp totals
+    }
+    __syncthreads();
+    uint32_t run = x - sum + (w > 0 ? scratch[w - 1] : 0);
+    const uint32_t total = scratch[(nt >> 5) - 1];
+    for (int i = lo; i < hi; ++i) {
+        uint32_t c = a[i];
+        a[i] = run;
+        run += c;
+    }
+    __syncthreads();
+    return total;
+}
+
+// ---------------------------------------------------------------------------
+// Step 2 of SqRan: sample positions floor(u_j n / 2^64), u_j = output j of
+// stream 1 of SplitMix64 keyed by seed.
+// ---------------------------------------------------------------------------
+static __global__ void k_ran_positions(uint32_t* pos, uint32_t m, uint64_t n, uint64_t seed) {
+    const uint64_t state = sm_stream(seed, 1);
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x)
+        pos[j] = (uint32_t)__umul64hi(sm_at(state, j), n);
+}
+
+// T_j = (keys[pos_j], tag pos_j)
+template <class KT>
+__global__ void k_gather_tagged(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ pos,
+                                uint32_t m, typename KT::T* tk, uint32_t* tt) {
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+        const uint32_t q = pos[j];
+        tk[j] = keys[q];
+        tt[j] = q;
+    }
+}
+
+// Step 2 of SqDet: sequence k = [floor(kn/p), floor((k+1)n/p)) of the sorted
+// sequences A gives mm = r p samples; sample j (1..mm) is its key of local rank
+// ceil(j c / mm) - 1 (the ends of mm near-equal segments; j = mm is the max).
+// The tag is the position in A, i.e. start_k + local rank.
+template <class KT>
+__global__ void k_det_sample(const typename KT::T* __restrict__ A, uint64_t n, uint32_t p, uint32_t mm,
+                             typename KT::T* tk, uint32_t* tt) {
+    const uint64_t total = (uint64_t)p * mm;
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < total;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = q / mm, j = q % mm + 1;
+        const uint64_t cs = k * n / p, c = (k + 1) * n / p - cs;
+        const uint64_t l = (j * c + mm - 1) / mm - 1;
+        tk[q] = A[cs + l];
+        tt[q] = (uint32_t)(cs + l);
+    }
+}
+
+// Step 3: S_i = the (i * stride)-th smallest of the sorted sample, i = 1..p-1.
+template <class KT>
+__global__ void k_pick_splitters(const typename KT::T* __restrict__ tk, const uint32_t* __restrict__ tt,
+                                 uint32_t p, uint64_t stride, typename KT::O* spl_o, uint32_t* spl_t) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x + 1; i < p; i += gridDim.x * blockDim.x) {
+        const uint64_t q = (uint64_t)i * stride - 1;
+        spl_o[i - 1] = KT::ord(tk[q]);
+        spl_t[i - 1] = tt[q];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Step 4, pass 1: every CTA owns a contiguous run of tiles, finds the bucket of
+// each key (tag = its position in the array) and counts keys per bucket.
+// hist is bucket-major: hist[b * G + g].
+// ---------------------------------------------------------------------------
+__host__ __device__ inline uint32_t tile_lo(uint32_t g, uint32_t G, uint32_t ntiles) {
+    return (uint32_t)(((uint64_t)g * ntiles) / G);
+}
+
+template <class KT>
+__global__ void __launch_bounds__(TOP_NT)
+k_classify(const typename KT::T* __restrict__ keys, uint32_t n, const typename KT::O* __restrict__ spl_o,
+           const uint32_t* __restrict__ spl_t, int p, int h, uint32_t* __restrict__ hist, uint32_t ntiles) {
+    using O = typename KT::O;
+    extern __shared__ __align__(16) char smem[];
+    const int P = 1 << h;
+    Tree<O> tr;
+    tr.bind(smem, P);
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + Tree<O>::node_bytes * P);
+    tree_from_arrays<O>(tr, spl_o, spl_t, p, h);
+    for (int b = threadIdx.x; b < p; b += TOP_NT) cnt[b] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t G = gridDim.x, g = blockIdx.x;
+    const uint32_t t0 = tile_lo(g, G, ntiles), t1 = tile_lo(g + 1, G, ntiles);
+    for (uint32_t t = t0; t < t1; ++t) {
+        const uint32_t base = t * TOP_TILE + w * (TOP_IT * 32) + lane;
+        O o[TOP_IT];
+#pragma unroll
+        for (int i = 0; i < TOP_IT; ++i) {
+            const uint32_t e = base + i * 32;
+            o[i] = e < n ? KT::ord(keys[e]) : O(0);
+        }
+#pragma unroll
+        for (int i = 0; i < TOP_IT; ++i) {
+            const uint32_t e = base + i * 32;
+            const bool valid = e < n;
+            const unsigned act = __ballot_sync(0xffffffffu, valid);
+            if (valid) {
+                const int b = tr.find(o[i], e, h);
+                const unsigned m = __match_any_sync(act, b);
+                if (lane == __ffs(m) - 1) atomicAdd(&cnt[b], __popc(m));
+            }
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < p; b += TOP_NT) hist[(size_t)b * G + g] = cnt[b];
+}
+
+// Exclusive scan of every bucket's column of CTA counts (one warp per bucket),
+// and the bucket sizes.
+static __global__ void k_column_scan(const uint32_t* __restrict__ hist, uint32_t p, uint32_t G,
+                              uint32_t* __restrict__ col, uint32_t* __restrict__ bsize) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b >= p) return;
+    const uint32_t* h = hist + (size_t)b * G;
+    uint32_t* c = col + (size_t)b * G;
+    uint32_t carry = 0;
+    for (uint32_t g0 = 0; g0 < G; g0 += 32) {
+        const uint32_t g = g0 + lane;
+        const uint32_t x = g < G ? h[g] : 0;
+        uint32_t y = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += z;
+        }
+        if (g < G) c[g] = carry + y - x;
+        carry += __shfl_sync(0xffffffffu, y, 31);
+    }
+    if (lane == 0) bsize[b] = carry;
+}
+
+// Bucket start offsets (exclusive scan of the sizes; boff[p] = n) and the
+// largest bucket.  One block.
+static __global__ void k_bucket_offsets(const uint32_t* __restrict__ bsize, uint32_t p, uint32_t* __restrict__ boff,
+                                 uint32_t* __restrict__ maxb) {
+    __shared__ uint32_t buf[MAX_P + 1];
+    __shared__ uint32_t scratch[32];
+    uint32_t mx = 0;
+    for (uint32_t b = threadIdx.x; b < p; b += blockDim.x) {
+        buf[b] = bsize[b];
+        mx = max(mx, bsize[b]);
+    }
+    atomicMax(maxb, mx);
+    const uint32_t total = block_exclusive_scan(buf, (int)p, scratch);
+    for (uint32_t b = threadIdx.x; b < p; b += blockDim.x) boff[b] = buf[b];
+    if (threadIdx.x == 0) boff[p] = total;
+}
+
+// ---------------------------------------------------------------------------
+// Step 4, pass 2: the same CTAs walk the same tiles in order, find each key's
+// bucket again and move the keys (and payloads) into their buckets.  Inside a
+// tile a key's rank among the tile's keys of its bucket comes from per-warp
+// counters (__match_any_sync groups) plus a cross-warp prefix, so every bucket
+// receives its keys in input order (a stable scatter).  Keys are staged in
+// shared memory grouped by bucket and written out as contiguous runs.
+// ---------------------------------------------------------------------------
+template <class KT, bool HV>
+__global__ void __launch_bounds__(TOP_NT)
+k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ vals, uint32_t n,
+          const typename KT::O* __restrict__ spl_o, const uint32_t* __restrict__ spl_t, int p, int h,
+          const uint32_t* __restrict__ col, const uint32_t* __restrict__ boff, typename KT::T* __restrict__ out,
+          uint32_t* __restrict__ vout, uint32_t ntiles) {
+    using O = typename KT::O;
+    using T = typename KT::T;
+    extern __shared__ __align__(16) char smem[];
+    const int P = 1 << h;
+    Tree<O> tr;
+    tr.bind(smem, P);
+    char* q = smem + ((Tree<O>::node_bytes * P + 15) & ~15);
+    T* sk = reinterpret_cast<T*>(q);                 q += sizeof(T) * TOP_TILE;
+    uint32_t* sv = reinterpret_cast<uint32_t*>(q);    q += HV ? sizeof(uint32_t) * TOP_TILE : 0;
+    uint32_t* tile_off = reinterpret_cast<uint32_t*>(q); q += sizeof(uint32_t) * (p + 1);
+    uint32_t* cursor = reinterpret_cast<uint32_t*>(q);   q += sizeof(uint32_t) * p;
+    uint32_t* scratch = reinterpret_cast<uint32_t*>(q);  q += sizeof(uint32_t) * 32;
+    uint16_t* sb = reinterpret_cast<uint16_t*>(q);       q += sizeof(uint16_t) * TOP_TILE;
+    uint16_t* cnt = reinterpret_cast<uint16_t*>(q);      // [TOP_WARPS][p + 1]
+    const int cstride = p + 1;
+
+    const uint32_t G = gridDim.x, g = blockIdx.x;
+    tree_from_arrays<O>(tr, spl_o, spl_t, p, h);
+    for (int b = threadIdx.x; b < p; b += TOP_NT) cursor[b] = boff[b] + col[(size_t)b * G + g];
+
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint16_t* mycnt = cnt + w * cstride;
+    const uint32_t t0 = tile_lo(g, G, ntiles), t1 = tile_lo(g + 1, G, ntiles);
+    for (uint32_t t = t0; t < t1; ++t) {
+        const uint32_t tbase = t * TOP_TILE;
+        const uint32_t base = tbase + w * (TOP_IT * 32) + lane;
+        T kv[TOP_IT];
+        uint32_t br[TOP_IT];   // bucket << 16 | rank inside the warp
+#pragma unroll
+        for (int i = 0; i < TOP_IT; ++i) {
+            const uint32_t e = base + i * 32;
+            kv[i] = e < n ? keys[e] : T(0);
+        }
+        for (int b = lane; b <= p; b += 32) mycnt[b] = 0;
+        __syncthreads();   // tree/cursors ready; previous tile fully written out
+#pragma unroll
+        for (int i = 0; i < TOP_IT; ++i) {
+            const uint32_t e = base + i * 32;
+            const bool valid = e < n;
+            const int b = valid ? tr.find(KT::ord(kv[i]), e, h) : p;
+            const unsigned m = __match_any_sync(0xffffffffu, b);
+            const uint32_t c0 = mycnt[b];
+            br[i] = ((uint32_t)b << 16) | (c0 + __popc(m & lanemask_lt()));
+            __syncwarp();
+            if (lane == __ffs(m) - 1) mycnt[b] = (uint16_t)(c0 + __popc(m));
+            __syncwarp();
+        }
+        __syncthreads();
+        // Cross-warp exclusive prefix per bucket; tile totals into tile_off.
+        for (int b = threadIdx.x; b < p; b += TOP_NT) {
+            uint32_t run = 0;
+#pragma unroll
+            for (int ww = 0; ww < TOP_WARPS; ++ww) {
+                const uint32_t c = cnt[ww * cstride + b];
+                cnt[ww * cstride + b] = (uint16_t)run;
+                run += c;
+            }
+            tile_off[b] = run;
+        }
+        const uint32_t tvalid = block_exclusive_scan(tile_off, p, scratch);
+        if (threadIdx.x == 0) tile_off[p] = tvalid;
+        // Stage keys grouped by bucket.
+#pragma unroll
+        for (int i = 0; i < TOP_IT; ++i) {
+            const int b = (int)(br[i] >> 16);
+            if (b < p) {
+                const uint32_t loc = tile_off[b] + mycnt[b] + (br[i] & 0xFFFFu);
+                sk[loc] = kv[i];
+                if (HV) sv[loc] = vals[base + i * 32];
+                sb[loc] = (uint16_t)b;
+            }
+        }
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < tvalid; j += TOP_NT) {
+            const int b = sb[j];
+            const uint32_t dst = cursor[b] + (j - tile_off[b]);
+            out[dst] = sk[j];
+            if (HV) vout[dst] = sv[j];
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < p; b += TOP_NT) cursor[b] += tile_off[b + 1] - tile_off[b];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Step 5 (and step 1 of SqDet): sort every segment of an array.
+// A segment of at most CAP keys is sorted in shared memory by one CTA
+// (k_leaf, block_merge_sort).  A larger one is repartitioned by one CTA
+// (k_repart) -- the recursion on the split keys "by this same method" of the
+// paper's introduction: a stratified random sample of SAMPLE2 tagged keys gives
+// p2 - 1 splitters (tag = position inside the segment), a counting pass and a
+// stable scatter move the keys into p2 child segments in another buffer, and
+// the children go to the leaf list or to the next level's list.
+// Buffers: id 0 = src (level-0 data, never written), 1 = other, 2 = alt.
+// Children of a level-d repartition are written to `other` (d even) or `alt`
+// (d odd); leaves always write the sorted keys to `out`.
+// ---------------------------------------------------------------------------
+struct SegSpec {
+    const uint32_t* off;   // segment offsets [nseg + 1], or nullptr for uniform segments
+    uint32_t nseg;
+    uint64_t n;            // uniform: segment k = [floor(kn/nseg), floor((k+1)n/nseg))
+};
+
+__device__ __forceinline__ void seg_bounds(const SegSpec& ss, uint32_t k, uint32_t& beg, uint32_t& len) {
+    if (ss.off) {
+        beg = ss.off[k];
+        len = ss.off[k + 1] - beg;
+    } else {
+        const uint64_t a = (uint64_t)k * ss.n / ss.nseg, b = (uint64_t)(k + 1) * ss.n / ss.nseg;
+        beg = (uint32_t)a;
+        len = (uint32_t)(b - a);
+    }
+}
+
+template <class KT, bool HV>
+struct BucketSmem {
+    using O = typename KT::O;
+    static constexpr int IT = LeafIT<O>::v;
+    static constexpr int CAP = Cap<O>::v;
+    static constexpr size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+    static constexpr size_t sk_bytes = al16(sizeof(O) * padded_len<O>(CAP));
+    static constexpr size_t sv_bytes = al16(sizeof(uint32_t) * padded_len<uint32_t>(CAP));
+    static constexpr size_t sb_bytes = al16(sizeof(uint16_t) * CAP);
+    static constexpr size_t tree_bytes = al16(Tree<O>::node_bytes * MAXP2);
+    static constexpr size_t cnt_bytes = al16(sizeof(uint16_t) * BK_WARPS * (MAXP2 + 1));
+    static constexpr size_t small_bytes = sizeof(uint32_t) * (4 * (MAXP2 + 1) + 32);
+    static constexpr size_t bytes = sk_bytes + sv_bytes + sb_bytes + tree_bytes + cnt_bytes + small_bytes + 64;
+    static constexpr size_t leaf_bytes = sk_bytes + sv_bytes;
+};
+
+template <class KT, bool HV>
+__device__ void leaf_sort(const typename KT::T* in, const uint32_t* vin, typename KT::T* out, uint32_t* vout,
+                          uint32_t beg, uint32_t len, typename KT::O* sk, uint32_t* sv) {
+    using O = typename KT::O;
+    constexpr int IT = LeafIT<O>::v;
+    const int ext = sort_extent<IT>((int)len);
+    for (int j = threadIdx.x; j < ext; j += BK_NT) {
+        sk[pad_idx<O>(j)] = j < (int)len ? KT::ord(in[beg + j]) : OMax<O>::v;
+        if (HV) sv[pad_idx<uint32_t>(j)] = j < (int)len ? vin[beg + j] : 0u;
+    }
+    block_merge_sort<O, HV, BK_NT, IT>(sk, sv, ext);
+    for (int j = threadIdx.x; j < (int)len; j += BK_NT) {
+        out[beg + j] = KT::key(sk[pad_idx<O>(j)]);
+        if (HV) vout[beg + j] = sv[pad_idx<uint32_t>(j)];
+    }
+    __syncthreads();
+}
+
+// Repartition [beg, beg+len) of `in` into p2 children written to `outb`; child
+// offsets (relative to beg) go to off[0..p2].  Returns p2.
+template <class KT, bool HV>
+__device__ int cta_partition(const typename KT::T* in, const uint32_t* vin, typename KT::T* outb, uint32_t* voutb,
+                             uint32_t beg, uint32_t len, int level, uint64_t seed, char* smem_base,
+                             uint32_t* off) {
+    using O = typename KT::O;
+    using T = typename KT::T;
+    using L = BucketSmem<KT, HV>;
+    constexpr int IT = 8;                 // keys per thread in the two passes (lower register use)
+    constexpr int TILE = BK_NT * IT;
+    constexpr int CAP = L::CAP;
+    char* q = smem_base;
+    O* sk = reinterpret_cast<O*>(q);               q += L::sk_bytes;
+    uint32_t* sv = reinterpret_cast<uint32_t*>(q); q += L::sv_bytes;
+    uint16_t* sb = reinterpret_cast<uint16_t*>(q); q += L::sb_bytes;
+    Tree<O> tr;
+    tr.bind(q, MAXP2);                              q += L::tree_bytes;
+    uint16_t* cnt = reinterpret_cast<uint16_t*>(q); q += L::cnt_bytes;
+    uint32_t* part = reinterpret_cast<uint32_t*>(q);     q += sizeof(uint32_t) * (MAXP2 + 1);
+    uint32_t* tile_off = reinterpret_cast<uint32_t*>(q); q += sizeof(uint32_t) * (MAXP2 + 1);
+    uint32_t* cursor = reinterpret_cast<uint32_t*>(q);   q += sizeof(uint32_t) * (MAXP2 + 1);
+    uint32_t* scratch = reinterpret_cast<uint32_t*>(q);
+
+    // Fan-out: children of about 5/8 CAP on average, at most MAXP2.
+    int p2 = 2;
+    while (p2 < MAXP2 && (uint64_t)p2 * (CAP * 5 / 8) < len) p2 <<= 1;
+    int h = 31 - __clz(p2);
+    const int s2 = SAMPLE2 / p2;
+    const int m2 = p2 * s2;
+
+    // 1. Stratified random sample: one key from each of m2 near-equal strata,
+    //    tagged with its position (strata are in position order, so a stable
+    //    sort by key leaves the sample in tagged order).
+    const uint64_t state = sm_stream(seed ^ ((uint64_t)beg * SM_GAMMA), 2 + level);
+    for (int j = threadIdx.x; j < m2; j += BK_NT) {
+        const uint32_t lo = (uint32_t)((uint64_t)j * len / m2);
+        const uint32_t hi = (uint32_t)((uint64_t)(j + 1) * len / m2);
+        const uint32_t pos = lo + (uint32_t)(sm_at(state, j) % (uint64_t)(hi - lo));
+        sk[pad_idx<O>(j)] = KT::ord(in[beg + pos]);
+        sv[pad_idx<uint32_t>(j)] = pos;
+    }
+    static_assert(SAMPLE2 == BK_NT * IT, "the sample is sorted as one block of BK_NT x IT keys");
+    block_merge_sort<O, true, BK_NT, IT>(sk, sv, m2);
+    for (int v = threadIdx.x + 1; v < p2; v += BK_NT) {
+        const int i = eytz_rank(v, h);
+        tr.set(v, sk[pad_idx<O>(i * s2 - 1)], sv[pad_idx<uint32_t>(i * s2 - 1)]);
+    }
+    for (int b = threadIdx.x; b <= p2; b += BK_NT) part[b] = 0;
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // 2. Counting pass.
+    for (uint32_t tb = 0; tb < len; tb += TILE) {
+        const uint32_t base = tb + w * (IT * 32) + lane;
+        O o[IT];
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const uint32_t e = base + i * 32;
+            o[i] = e < len ? KT::ord(in[beg + e]) : O(0);
+        }
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const uint32_t e = base + i * 32;
+            const bool valid = e < len;
+            const unsigned act = __ballot_sync(0xffffffffu, valid);
+            if (valid) {
+                const int b = tr.find(o[i], e, h);
+                const unsigned m = __match_any_sync(act, b);
+                if (lane == __ffs(m) - 1) atomicAdd(&part[b], __popc(m));
+            }
+        }
+    }
+    const uint32_t total = block_exclusive_scan(part, p2, scratch);
+    for (int b = threadIdx.x; b < p2; b += BK_NT) {
+        off[b] = part[b];
+        cursor[b] = beg + part[b];
+    }
+    if (threadIdx.x == 0) off[p2] = total;
+    // 3. Stable scatter pass (same ranking scheme as k_scatter).
+    const int cstride = MAXP2 + 1;
+    uint16_t* mycnt = cnt + w * cstride;
+    for (uint32_t tb = 0; tb < len; tb += TILE) {
+        const uint32_t base = tb + w * (IT * 32) + lane;
+        T kv[IT];
+        uint32_t br[IT];   // bucket << 16 | rank inside the warp
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const uint32_t e = base + i * 32;
+            kv[i] = e < len ? in[beg + e] : T(0);
+        }
+        for (int b = lane; b <= p2; b += 32) mycnt[b] = 0;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const uint32_t e = base + i * 32;
+            const bool valid = e < len;
+            const int b = valid ? tr.find(KT::ord(kv[i]), e, h) : p2;
+            const unsigned m = __match_any_sync(0xffffffffu, b);
+            const uint32_t c0 = mycnt[b];
+            br[i] = ((uint32_t)b << 16) | (c0 + __popc(m & lanemask_lt()));
+            __syncwarp();
+            if (lane == __ffs(m) - 1) mycnt[b] = (uint16_t)(c0 + __popc(m));
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < p2; b += BK_NT) {
+            uint32_t run = 0;
+#pragma unroll
+            for (int ww = 0; ww < BK_WARPS; ++ww) {
+                const uint32_t c = cnt[ww * cstride + b];
+                cnt[ww * cstride + b] = (uint16_t)run;
+                run += c;
+            }
+            tile_off[b] = run;
+        }
+        const uint32_t tvalid = block_exclusive_scan(tile_off, p2, scratch);
+        if (threadIdx.x == 0) tile_off[p2] = tvalid;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const int b = (int)(br[i] >> 16);
+            if (b < p2) {
+                const uint32_t loc = tile_off[b] + mycnt[b] + (br[i] & 0xFFFFu);
+                sk[loc] = KT::ord(kv[i]);
+                if (HV) sv[loc] = vin[beg + base + i * 32];
+                sb[loc] = (uint16_t)b;
+            }
+        }
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < tvalid; j += BK_NT) {
+            const int b = sb[j];
+            const uint32_t dst = cursor[b] + (j - tile_off[b]);
+            outb[dst] = KT::key(sk[j]);
+            if (HV) voutb[dst] = sv[j];
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < p2; b += BK_NT) cursor[b] += tile_off[b + 1] - tile_off[b];
+    }
+    __syncthreads();
+    return p2;
+}
+
+struct WorkItem {
+    uint32_t beg, len, buf, pad;
+};
+
+template <class KT>
+struct SortBufs {
+    typename KT::T* k[3];
+    uint32_t* v[3];
+    typename KT::T* out;
+    uint32_t* vout;
+    // constant-index selection keeps the pointers in parameter space
+    __device__ __forceinline__ typename KT::T* key_buf(uint32_t id) const { return id == 0 ? k[0] : (id == 1 ? k[1] : k[2]); }
+    __device__ __forceinline__ uint32_t* val_buf(uint32_t id) const { return id == 0 ? v[0] : (id == 1 ? v[1] : v[2]); }
+};
+
+struct WorkLists {
+    WorkItem* leaf;       // leaves of every level
+    uint32_t leaf_cap;
+    WorkItem* part[2];    // segments to repartition, alternating by level parity
+    uint32_t part_cap;
+    uint32_t* counts;     // [0] leaves, [1 + d] segments of level d
+};
+
+__device__ __forceinline__ void push_item(WorkItem* list, uint32_t* count, uint32_t cap, uint32_t beg, uint32_t len,
+                                          uint32_t buf, uint32_t* status) {
+    const uint32_t i = atomicAdd(count, 1u);
+    if (i < cap) list[i] = WorkItem{beg, len, buf, 0u};
+    else atomicOr(status, ERR_SIZES);
+}
+
+// One repartition level.  Level 0 walks the segments of ss; level d >= 1 walks
+// the list filled by level d - 1.  Persistent: CTAs stride over the work.
+template <class KT, bool HV>
+__global__ void __launch_bounds__(BK_NT, 2)
+k_repart(int level, SegSpec ss, SortBufs<KT> bufs, WorkLists wl, uint64_t seed, uint32_t* status,
+         uint32_t* depth_max, unsigned long long* moved) {
+    using O = typename KT::O;
+    using L = BucketSmem<KT, HV>;
+    extern __shared__ __align__(16) char smem[];
+    uint32_t* off = reinterpret_cast<uint32_t*>(smem + L::bytes - sizeof(uint32_t) * (MAXP2 + 1) - 16);
+    const uint32_t nwork = level == 0 ? ss.nseg : min(wl.counts[level], wl.part_cap);
+    const WorkItem* in_list = wl.part[(level - 1) & 1];
+    WorkItem* next_list = wl.part[level & 1];
+    const uint32_t outbuf = (level & 1) ? 2u : 1u;
+    for (uint32_t it = blockIdx.x; it < nwork; it += gridDim.x) {
+        uint32_t beg, len, inbuf;
+        if (level == 0) {
+            seg_bounds(ss, it, beg, len);
+            inbuf = 0;
+        } else {
+            const WorkItem w = in_list[it];
+            beg = w.beg;
+            len = w.len;
+            inbuf = w.buf;
+        }
+        if (len == 0) continue;
+        if (len <= (uint32_t)L::CAP) {
+            if (threadIdx.x == 0) push_item(wl.leaf, &wl.counts[0], wl.leaf_cap, beg, len, inbuf, status);
+            continue;
+        }
+        const int p2 = cta_partition<KT, HV>(bufs.key_buf(inbuf), bufs.val_buf(inbuf), bufs.key_buf(outbuf),
+                                             bufs.val_buf(outbuf), beg, len, level, seed, smem, off);
+        if (threadIdx.x == 0) {
+            atomicMax(depth_max, (uint32_t)(level + 1));
+            atomicAdd(moved, (unsigned long long)len);
+        }
+        for (int b = threadIdx.x; b < p2; b += BK_NT) {
+            const uint32_t cb = beg + off[b], cl = off[b + 1] - off[b];
+            if (cl == 0) continue;
+            if (cl <= (uint32_t)L::CAP) push_item(wl.leaf, &wl.counts[0], wl.leaf_cap, cb, cl, outbuf, status);
+            else if (level + 1 < MAX_DEPTH)
+                push_item(next_list, &wl.counts[level + 1], wl.part_cap, cb, cl, outbuf, status);
+            else atomicOr(status, ERR_DEPTH);
+        }
+        __syncthreads();
+    }
+}
+
+// Shared-memory sort of every leaf: the segments of ss directly (direct = true)
+// or the leaf list.  Persistent: CTAs stride over the work.
+template <class KT, bool HV>
+__global__ void __launch_bounds__(BK_NT, 2)
+k_leaf(bool direct, SegSpec ss, SortBufs<KT> bufs, WorkLists wl) {
+    using O = typename KT::O;
+    using L = BucketSmem<KT, HV>;
+    extern __shared__ __align__(16) char smem[];
+    O* sk = reinterpret_cast<O*>(smem);
+    uint32_t* sv = reinterpret_cast<uint32_t*>(smem + L::sk_bytes);
+    const uint32_t nwork = direct ? ss.nseg : min(wl.counts[0], wl.leaf_cap);
+    for (uint32_t it = blockIdx.x; it < nwork; it += gridDim.x) {
+        uint32_t beg, len, buf;
+        if (direct) {
+            seg_bounds(ss, it, beg, len);
+            buf = 0;
+        } else {
+            const WorkItem w = wl.leaf[it];
+            beg = w.beg;
+            len = w.len;
+            buf = w.buf;
+        }
+        if (len == 0) continue;
+        leaf_sort<KT, HV>(bufs.key_buf(buf), bufs.val_buf(buf), bufs.out, bufs.vout, beg, len, sk, sv);
+    }
+}
+
+}  // namespace ossort

@@ -1,0 +1,7 @@
+// Instantiation of the sort for one key type (one translation unit per type
+// so the build compiles them in parallel).
+#include "driver.cuh"
+
+namespace ossort {
+int run_i32(RunArgs& a) { return run_sort<KeyI32>(a); }
+}  // namespace ossort
