@@ -1,6 +1,8 @@
 // The C ABI of include/ossort.h: argument checks, workspace planning, dispatch
 // on the key type, statistics and the host-buffer variant.
 #include <atomic>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -46,7 +48,17 @@ void prof_before(cudaStream_t st, const char* name) {
     g_pending_a = pool_event();
     cudaEventRecord(g_pending_a, st);
 }
-void prof_after(cudaStream_t st) {
+void prof_after(cudaStream_t st, const char* name) {
+    static const bool debug_sync = [] {
+        const char* e = std::getenv("OSSORT_DEBUG_SYNC");
+        return e && e[0] == '1';
+    }();
+    if (debug_sync) {
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) std::fprintf(stderr, "ossort: kernel %s failed: %s\n", name, cudaGetErrorString(e));
+        else std::fprintf(stderr, "ossort: kernel %s ok\n", name);
+    }
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_prof_on || !g_pending_a) return;
     cudaEvent_t b = pool_event();
@@ -256,7 +268,8 @@ int os_sort(int key_type, const void* d_keys_in, void* d_keys_out, const uint32_
     a.ws_bytes = ws_bytes;
     a.st = static_cast<cudaStream_t>(stream);
     a.num_sms = num_sms_of_current_device();
-    dispatch(key_type, a);
+    rc = dispatch(key_type, a);
+    if (rc) return rc;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
     if (stats) return fill_stats(key_type, a, a.st, stats);

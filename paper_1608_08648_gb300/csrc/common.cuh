@@ -91,21 +91,39 @@ template <class O> struct Cap { static constexpr int v = BK_NT * LeafIT<O>::v; }
 constexpr uint32_t ERR_DEPTH = 1u;         // a bucket still too large at MAX_DEPTH
 constexpr uint32_t ERR_SIZES = 2u;         // a work list overflowed
 constexpr uint32_t ERR_SAMPLE = 4u;        // sample larger than its buffer
+constexpr uint32_t ERR_BOUNDS = 8u;        // an index failed its range check (access skipped)
+
+// Record a failed range check in the status word: the error bit, the first
+// failing site in status[6] and its index in status[7].  The access is skipped
+// by the caller, so a wrong index never touches memory outside its buffer.
+__device__ __forceinline__ void flag_bounds(uint32_t* status, uint32_t site, uint64_t idx) {
+    atomicOr(status, ERR_BOUNDS);
+    if (atomicCAS(status + 6, 0u, site) == 0u) status[7] = (uint32_t)idx;
+}
 
 // ---------------------------------------------------------------------------
 // Workspace arena: a bump allocator over the caller's workspace.  In measure
 // mode (base == nullptr) it only adds up sizes, so os_workspace_size runs the
-// same planning code as os_sort.
+// same planning code as os_sort.  Measure mode hands out distinct non-null
+// placeholder addresses (never dereferenced: no kernel is launched while
+// measuring), so a decision that looks at a pointer takes the same branch in
+// both modes.  A live request beyond the capacity sets `failed`, after which
+// nothing more is launched and the sort reports a workspace error.
 // ---------------------------------------------------------------------------
 struct Arena {
     char* base = nullptr;
     size_t cap = 0;
     size_t used = 0;
+    bool failed = false;
     bool measure() const { return base == nullptr; }
     template <class X> X* take(size_t count) {
         size_t off = (used + 255) & ~size_t(255);
         used = off + count * sizeof(X);
-        if (measure() || used > cap) return nullptr;
+        if (measure()) return reinterpret_cast<X*>(static_cast<uintptr_t>(0x10000) + off);
+        if (used > cap) {
+            failed = true;
+            return nullptr;
+        }
         return reinterpret_cast<X*>(base + off);
     }
 };

@@ -25,7 +25,7 @@ struct Ctx {
     int num_sms = 152;
     uint32_t* status = nullptr;   // [0] error bits, [1] depth, [2] max bucket, [4..5] u64 repartitioned keys
     bool nested = false;          // inside the sort of a sample (launch names get a ".sample" suffix)
-    bool live() const { return !ar.measure(); }
+    bool live() const { return !ar.measure() && !ar.failed; }
 };
 
 inline uint32_t pow2_ceil(uint32_t x) {
@@ -74,7 +74,7 @@ void segment_sort(Ctx& c, SegSpec ss, const typename KT::T* src, const uint32_t*
     bufs.out = out;
     bufs.vout = vout;
     WorkLists wl{};
-    const bool direct = ss.off == nullptr && (ss.n + ss.nseg - 1) / ss.nseg <= CAP;
+    const bool direct = ss.uniform && (ss.n + ss.nseg - 1) / ss.nseg <= CAP;
     if (!direct) {
         wl.counts = c.ar.take<uint32_t>(MAX_DEPTH + 1);
         wl.part_cap = (uint32_t)(ss.n / CAP + 1);
@@ -88,10 +88,10 @@ void segment_sort(Ctx& c, SegSpec ss, const typename KT::T* src, const uint32_t*
     const uint32_t grid_l = (uint32_t)(c.num_sms * occupancy(k_leaf<KT, HV>, BK_NT, L::leaf_bytes));
     if (direct) {
         OS_LAUNCH(c.st, c.nested ? "k_leaf.sample" : "k_leaf",
-                  k_leaf<KT, HV><<<std::min(ss.nseg, grid_l), BK_NT, L::leaf_bytes, c.st>>>(true, ss, bufs, wl));
+                  k_leaf<KT, HV><<<std::min(ss.nseg, grid_l), BK_NT, L::leaf_bytes, c.st>>>(true, ss, bufs, wl, c.status));
         return;
     }
-    cudaMemsetAsync(wl.counts, 0, sizeof(uint32_t) * (MAX_DEPTH + 1), c.st);
+    os_memset_async(wl.counts, 0, sizeof(uint32_t) * (MAX_DEPTH + 1), c.st);
     cudaFuncSetAttribute(k_repart<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
     const uint32_t grid_r = (uint32_t)(c.num_sms * occupancy(k_repart<KT, HV>, BK_NT, L::bytes));
     for (int level = 0; level < MAX_DEPTH; ++level) {
@@ -100,7 +100,7 @@ void segment_sort(Ctx& c, SegSpec ss, const typename KT::T* src, const uint32_t*
                   k_repart<KT, HV><<<g, BK_NT, L::bytes, c.st>>>(level, ss, bufs, wl, seed, c.status, c.status + 1,
                                                                  reinterpret_cast<unsigned long long*>(c.status + 4)));
     }
-    OS_LAUNCH(c.st, c.nested ? "k_leaf.sample" : "k_leaf", k_leaf<KT, HV><<<grid_l, BK_NT, L::leaf_bytes, c.st>>>(false, ss, bufs, wl));
+    OS_LAUNCH(c.st, c.nested ? "k_leaf.sample" : "k_leaf", k_leaf<KT, HV><<<grid_l, BK_NT, L::leaf_bytes, c.st>>>(false, ss, bufs, wl, c.status));
 }
 
 template <class KT>
@@ -144,7 +144,7 @@ void partition_top(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, uint
     OS_LAUNCH(c.st, c.nested ? "k_bucket_offsets.sample" : "k_bucket_offsets", k_bucket_offsets<<<1, 1024, 0, c.st>>>(bsize, p, boff, c.status + 2));
     OS_LAUNCH(c.st, c.nested ? "k_scatter.sample" : "k_scatter",
               k_scatter<KT, HV><<<G, TOP_NT, sm_s, c.st>>>(src, vsrc, n, spl_o, spl_t, (int)p, h, col, boff, dst,
-                                                           vdst, ntiles));
+                                                           vdst, ntiles, c.status));
 }
 
 template <class KT, bool HV>
@@ -174,7 +174,7 @@ void splitters_ran(Ctx& c, const typename KT::T* keys, uint32_t n, uint32_t p, u
     sort_array<KeyU32, false>(c, pos, nullptr, pos_s, nullptr, m, sm_mix(seed ^ 0x51ull));
     if (c.live())
         OS_LAUNCH(c.st, "k_gather_tagged",
-                  k_gather_tagged<KT><<<grid_for(m, 256, 1024), 256, 0, c.st>>>(keys, pos_s, m, tk, tt));
+                  k_gather_tagged<KT><<<grid_for(m, 256, 1024), 256, 0, c.st>>>(keys, n, pos_s, m, tk, tt, c.status));
     sort_array<KT, true>(c, tk, tt, tks, tts, m, sm_mix(seed ^ 0x52ull));
     c.nested = was_nested;
     if (c.live() && p > 1)
@@ -195,7 +195,7 @@ void splitters_det(Ctx& c, const typename KT::T* A, uint32_t n, uint32_t p, uint
     T* tks = c.ar.take<T>(m);
     uint32_t* tts = c.ar.take<uint32_t>(m);
     if (c.live())
-        OS_LAUNCH(c.st, "k_det_sample", k_det_sample<KT><<<grid_for(m, 256), 256, 0, c.st>>>(A, n, p, mm, tk, tt));
+        OS_LAUNCH(c.st, "k_det_sample", k_det_sample<KT><<<grid_for(m, 256), 256, 0, c.st>>>(A, n, p, mm, tk, tt, c.status));
     const bool was_nested = c.nested;
     c.nested = true;
     sort_array<KT, true>(c, tk, tt, tks, tts, (uint32_t)m, sm_mix(seed ^ 0x53ull));
@@ -216,7 +216,7 @@ void sort_array(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, typenam
     constexpr uint32_t CAP = (uint32_t)Cap<O>::v;
     if (n == 0) return;
     if (n <= CAP) {
-        segment_sort<KT, HV>(c, SegSpec{nullptr, 1, n}, src, vsrc, nullptr, nullptr, nullptr, nullptr, out, vout,
+        segment_sort<KT, HV>(c, SegSpec::even(1, n), src, vsrc, nullptr, nullptr, nullptr, nullptr, out, vout,
                              seed);
         return;
     }
@@ -230,7 +230,7 @@ void sort_array(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, typenam
     uint32_t* vw = HV ? c.ar.take<uint32_t>(n) : nullptr;
     splitters_ran<KT>(c, src, n, p, s, seed, spl_o, spl_t);
     partition_top<KT, HV>(c, src, vsrc, n, spl_o, spl_t, p, w, vw, boff, bsize);
-    segment_sort<KT, HV>(c, SegSpec{boff, p, n}, w, vw, out, vout, w, vw, out, vout, sm_mix(seed ^ 0x54ull));
+    segment_sort<KT, HV>(c, SegSpec::offsets(boff, p, n), w, vw, out, vout, w, vw, out, vout, sm_mix(seed ^ 0x54ull));
 }
 
 // Device results of one user-level sort (for statistics).
@@ -269,15 +269,15 @@ void sort_top(Ctx& c, const typename KT::T* kin, typename KT::T* kout, const uin
     if (prm.split == OS_RAN) {
         splitters_ran<KT>(c, kin, n, p, s, prm.seed, spl_o, spl_t);
         partition_top<KT, HV>(c, kin, vin, n, spl_o, spl_t, p, w1, vw1, boff, bsize);
-        segment_sort<KT, HV>(c, SegSpec{boff, p, n}, w1, vw1, kout, vout, w1, vw1, kout, vout, internal_seed);
+        segment_sort<KT, HV>(c, SegSpec::offsets(boff, p, n), w1, vw1, kout, vout, w1, vw1, kout, vout, internal_seed);
     } else {
         T* w2 = c.ar.take<T>(n);
         uint32_t* vw2 = HV ? c.ar.take<uint32_t>(n) : nullptr;
         // Step 1: the p sequences sorted into w1 (stable).
-        segment_sort<KT, HV>(c, SegSpec{nullptr, p, n}, kin, vin, w2, vw2, w1, vw1, w1, vw1, internal_seed);
+        segment_sort<KT, HV>(c, SegSpec::even(p, n), kin, vin, w2, vw2, w1, vw1, w1, vw1, internal_seed);
         splitters_det<KT>(c, w1, n, p, s, internal_seed, spl_o, spl_t);
         partition_top<KT, HV>(c, w1, vw1, n, spl_o, spl_t, p, w2, vw2, boff, bsize);
-        segment_sort<KT, HV>(c, SegSpec{boff, p, n}, w2, vw2, kout, vout, w2, vw2, kout, vout, internal_seed);
+        segment_sort<KT, HV>(c, SegSpec::offsets(boff, p, n), w2, vw2, kout, vout, w2, vw2, kout, vout, internal_seed);
     }
 }
 
@@ -309,14 +309,14 @@ int run_sort(RunArgs& a) {
     c.ar.base = static_cast<char*>(a.ws);
     c.ar.cap = a.ws_bytes;
     c.status = c.ar.take<uint32_t>(8);
-    if (c.live()) cudaMemsetAsync(c.status, 0, 8 * sizeof(uint32_t), c.st);
+    if (c.live()) os_memset_async(c.status, 0, 8 * sizeof(uint32_t), c.st);
     const T* kin = static_cast<const T*>(a.kin);
     T* kout = static_cast<T*>(a.kout);
     if (a.has_vals) sort_top<KT, true>(c, kin, kout, a.vin, a.vout, (uint32_t)a.n, a.prm, a.res);
     else sort_top<KT, false>(c, kin, kout, nullptr, nullptr, (uint32_t)a.n, a.prm, a.res);
     a.used = c.ar.used;
     a.status = c.status;
-    return 0;
+    return c.ar.failed ? OS_ERR_WS : OS_OK;
 }
 
 int run_i32(RunArgs& a);

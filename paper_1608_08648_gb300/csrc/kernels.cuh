@@ -133,10 +133,14 @@ static __global__ void k_ran_positions(uint32_t* pos, uint32_t m, uint64_t n, ui
 
 // T_j = (keys[pos_j], tag pos_j)
 template <class KT>
-__global__ void k_gather_tagged(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ pos,
-                                uint32_t m, typename KT::T* tk, uint32_t* tt) {
+__global__ void k_gather_tagged(const typename KT::T* __restrict__ keys, uint32_t n, const uint32_t* __restrict__ pos,
+                                uint32_t m, typename KT::T* tk, uint32_t* tt, uint32_t* status) {
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
         const uint32_t q = pos[j];
+        if (q >= n) {
+            flag_bounds(status, 1, q);
+            continue;
+        }
         tk[j] = keys[q];
         tt[j] = q;
     }
@@ -148,13 +152,17 @@ __global__ void k_gather_tagged(const typename KT::T* __restrict__ keys, const u
 // The tag is the position in A, i.e. start_k + local rank.
 template <class KT>
 __global__ void k_det_sample(const typename KT::T* __restrict__ A, uint64_t n, uint32_t p, uint32_t mm,
-                             typename KT::T* tk, uint32_t* tt) {
+                             typename KT::T* tk, uint32_t* tt, uint32_t* status) {
     const uint64_t total = (uint64_t)p * mm;
     for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < total;
          q += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t k = q / mm, j = q % mm + 1;
         const uint64_t cs = k * n / p, c = (k + 1) * n / p - cs;
         const uint64_t l = (j * c + mm - 1) / mm - 1;
+        if (c == 0 || cs + l >= n) {
+            flag_bounds(status, 2, cs + l);
+            continue;
+        }
         tk[q] = A[cs + l];
         tt[q] = (uint32_t)(cs + l);
     }
@@ -275,7 +283,7 @@ __global__ void __launch_bounds__(TOP_NT)
 k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ vals, uint32_t n,
           const typename KT::O* __restrict__ spl_o, const uint32_t* __restrict__ spl_t, int p, int h,
           const uint32_t* __restrict__ col, const uint32_t* __restrict__ boff, typename KT::T* __restrict__ out,
-          uint32_t* __restrict__ vout, uint32_t ntiles) {
+          uint32_t* __restrict__ vout, uint32_t ntiles, uint32_t* status) {
     using O = typename KT::O;
     using T = typename KT::T;
     extern __shared__ __align__(16) char smem[];
@@ -343,6 +351,10 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
             const int b = (int)(br[i] >> 16);
             if (b < p) {
                 const uint32_t loc = tile_off[b] + mycnt[b] + (br[i] & 0xFFFFu);
+                if (loc >= (uint32_t)TOP_TILE) {
+                    flag_bounds(status, 8, loc);
+                    continue;
+                }
                 sk[loc] = kv[i];
                 if (HV) sv[loc] = vals[base + i * 32];
                 sb[loc] = (uint16_t)b;
@@ -352,6 +364,10 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
         for (uint32_t j = threadIdx.x; j < tvalid; j += TOP_NT) {
             const int b = sb[j];
             const uint32_t dst = cursor[b] + (j - tile_off[b]);
+            if (dst >= n) {
+                flag_bounds(status, 3, dst);
+                continue;
+            }
             out[dst] = sk[j];
             if (HV) vout[dst] = sv[j];
         }
@@ -374,13 +390,16 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
 // (d odd); leaves always write the sorted keys to `out`.
 // ---------------------------------------------------------------------------
 struct SegSpec {
-    const uint32_t* off;   // segment offsets [nseg + 1], or nullptr for uniform segments
+    const uint32_t* off;   // segment offsets [nseg + 1] (unless uniform)
     uint32_t nseg;
-    uint64_t n;            // uniform: segment k = [floor(kn/nseg), floor((k+1)n/nseg))
+    uint32_t uniform;      // 1: segment k = [floor(kn/nseg), floor((k+1)n/nseg)); off unused
+    uint64_t n;            // length of the array the segments tile
+    static SegSpec offsets(const uint32_t* o, uint32_t nseg, uint64_t n) { return SegSpec{o, nseg, 0u, n}; }
+    static SegSpec even(uint32_t nseg, uint64_t n) { return SegSpec{nullptr, nseg, 1u, n}; }
 };
 
 __device__ __forceinline__ void seg_bounds(const SegSpec& ss, uint32_t k, uint32_t& beg, uint32_t& len) {
-    if (ss.off) {
+    if (!ss.uniform) {
         beg = ss.off[k];
         len = ss.off[k + 1] - beg;
     } else {
@@ -429,7 +448,7 @@ __device__ void leaf_sort(const typename KT::T* in, const uint32_t* vin, typenam
 template <class KT, bool HV>
 __device__ int cta_partition(const typename KT::T* in, const uint32_t* vin, typename KT::T* outb, uint32_t* voutb,
                              uint32_t beg, uint32_t len, int level, uint64_t seed, char* smem_base,
-                             uint32_t* off) {
+                             uint32_t* off, uint32_t* status) {
     using O = typename KT::O;
     using T = typename KT::T;
     using L = BucketSmem<KT, HV>;
@@ -462,7 +481,11 @@ __device__ int cta_partition(const typename KT::T* in, const uint32_t* vin, type
     for (int j = threadIdx.x; j < m2; j += BK_NT) {
         const uint32_t lo = (uint32_t)((uint64_t)j * len / m2);
         const uint32_t hi = (uint32_t)((uint64_t)(j + 1) * len / m2);
-        const uint32_t pos = lo + (uint32_t)(sm_at(state, j) % (uint64_t)(hi - lo));
+        uint32_t pos = lo + (uint32_t)(sm_at(state, j) % (uint64_t)max(hi - lo, 1u));
+        if (pos >= len) {
+            flag_bounds(status, 5, pos);
+            pos = 0;
+        }
         sk[pad_idx<O>(j)] = KT::ord(in[beg + pos]);
         sv[pad_idx<uint32_t>(j)] = pos;
     }
@@ -548,6 +571,10 @@ __device__ int cta_partition(const typename KT::T* in, const uint32_t* vin, type
             const int b = (int)(br[i] >> 16);
             if (b < p2) {
                 const uint32_t loc = tile_off[b] + mycnt[b] + (br[i] & 0xFFFFu);
+                if (loc >= (uint32_t)TILE) {
+                    flag_bounds(status, 9, loc);
+                    continue;
+                }
                 sk[loc] = KT::ord(kv[i]);
                 if (HV) sv[loc] = vin[beg + base + i * 32];
                 sb[loc] = (uint16_t)b;
@@ -557,6 +584,10 @@ __device__ int cta_partition(const typename KT::T* in, const uint32_t* vin, type
         for (uint32_t j = threadIdx.x; j < tvalid; j += BK_NT) {
             const int b = sb[j];
             const uint32_t dst = cursor[b] + (j - tile_off[b]);
+            if (dst < beg || dst - beg >= len) {
+                flag_bounds(status, 4, dst);
+                continue;
+            }
             outb[dst] = KT::key(sk[j]);
             if (HV) voutb[dst] = sv[j];
         }
@@ -627,8 +658,12 @@ k_repart(int level, SegSpec ss, SortBufs<KT> bufs, WorkLists wl, uint64_t seed, 
             if (threadIdx.x == 0) push_item(wl.leaf, &wl.counts[0], wl.leaf_cap, beg, len, inbuf, status);
             continue;
         }
+        if ((uint64_t)beg + len > ss.n) {
+            if (threadIdx.x == 0) flag_bounds(status, 7, (uint64_t)beg + len);
+            continue;
+        }
         const int p2 = cta_partition<KT, HV>(bufs.key_buf(inbuf), bufs.val_buf(inbuf), bufs.key_buf(outbuf),
-                                             bufs.val_buf(outbuf), beg, len, level, seed, smem, off);
+                                             bufs.val_buf(outbuf), beg, len, level, seed, smem, off, status);
         if (threadIdx.x == 0) {
             atomicMax(depth_max, (uint32_t)(level + 1));
             atomicAdd(moved, (unsigned long long)len);
@@ -649,7 +684,7 @@ k_repart(int level, SegSpec ss, SortBufs<KT> bufs, WorkLists wl, uint64_t seed, 
 // or the leaf list.  Persistent: CTAs stride over the work.
 template <class KT, bool HV>
 __global__ void __launch_bounds__(BK_NT, 2)
-k_leaf(bool direct, SegSpec ss, SortBufs<KT> bufs, WorkLists wl) {
+k_leaf(bool direct, SegSpec ss, SortBufs<KT> bufs, WorkLists wl, uint32_t* status) {
     using O = typename KT::O;
     using L = BucketSmem<KT, HV>;
     extern __shared__ __align__(16) char smem[];
@@ -668,6 +703,10 @@ k_leaf(bool direct, SegSpec ss, SortBufs<KT> bufs, WorkLists wl) {
             buf = w.buf;
         }
         if (len == 0) continue;
+        if (len > (uint32_t)L::CAP || (uint64_t)beg + len > ss.n) {
+            if (threadIdx.x == 0) flag_bounds(status, 6, (uint64_t)beg + len);
+            continue;
+        }
         leaf_sort<KT, HV>(bufs.key_buf(buf), bufs.val_buf(buf), bufs.out, bufs.vout, beg, len, sk, sv);
     }
 }
