@@ -137,13 +137,15 @@ int fill_stats(int kt, const RunArgs& a, cudaStream_t st, os_stats* stats) {
             stats->bucket_sizes[0] = a.n;
         }
     } else {
-        stats->max_bucket = status[2];
-        if (stats->bucket_sizes) {
-            std::vector<uint32_t> b(p);
-            e = cudaMemcpy(b.data(), a.res.bsize, p * sizeof(uint32_t), cudaMemcpyDeviceToHost);
-            if (e != cudaSuccess) return cuda_fail(e);
-            for (uint32_t j = 0; j < p; ++j) stats->bucket_sizes[j] = b[j];
+        std::vector<uint32_t> b(p);
+        e = cudaMemcpy(b.data(), a.res.bsize, p * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e);
+        uint64_t mx = 0;
+        for (uint32_t j = 0; j < p; ++j) {
+            if (stats->bucket_sizes) stats->bucket_sizes[j] = b[j];
+            mx = b[j] > mx ? b[j] : mx;
         }
+        stats->max_bucket = mx;
         if (stats->splitter_tags) {
             std::vector<uint32_t> t(p - 1);
             e = cudaMemcpy(t.data(), a.res.spl_t, (p - 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost);

@@ -23,7 +23,7 @@ struct Ctx {
     cudaStream_t st = nullptr;
     Arena ar;
     int num_sms = 152;
-    uint32_t* status = nullptr;   // [0] error bits, [1] depth, [2] max bucket, [4..5] u64 repartitioned keys
+    uint32_t* status = nullptr;   // [0] error bits, [1] depth, [4..5] u64 repartitioned keys, [6..7] range check
     bool nested = false;          // inside the sort of a sample (launch names get a ".sample" suffix)
     bool live() const { return !ar.measure() && !ar.failed; }
 };
@@ -141,7 +141,7 @@ void partition_top(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, uint
               k_classify<KT><<<G, TOP_NT, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, h, hist, ntiles));
     OS_LAUNCH(c.st, c.nested ? "k_column_scan.sample" : "k_column_scan",
               k_column_scan<<<grid_for((uint64_t)p * 32, 256), 256, 0, c.st>>>(hist, p, G, col, bsize));
-    OS_LAUNCH(c.st, c.nested ? "k_bucket_offsets.sample" : "k_bucket_offsets", k_bucket_offsets<<<1, 1024, 0, c.st>>>(bsize, p, boff, c.status + 2));
+    OS_LAUNCH(c.st, c.nested ? "k_bucket_offsets.sample" : "k_bucket_offsets", k_bucket_offsets<<<1, 1024, 0, c.st>>>(bsize, p, boff));
     OS_LAUNCH(c.st, c.nested ? "k_scatter.sample" : "k_scatter",
               k_scatter<KT, HV><<<G, TOP_NT, sm_s, c.st>>>(src, vsrc, n, spl_o, spl_t, (int)p, h, col, boff, dst,
                                                            vdst, ntiles, c.status));

@@ -253,18 +253,12 @@ static __global__ void k_column_scan(const uint32_t* __restrict__ hist, uint32_t
     if (lane == 0) bsize[b] = carry;
 }
 
-// Bucket start offsets (exclusive scan of the sizes; boff[p] = n) and the
-// largest bucket.  One block.
-static __global__ void k_bucket_offsets(const uint32_t* __restrict__ bsize, uint32_t p, uint32_t* __restrict__ boff,
-                                 uint32_t* __restrict__ maxb) {
+// Bucket start offsets: exclusive scan of the sizes; boff[p] = n.  One block.
+static __global__ void k_bucket_offsets(const uint32_t* __restrict__ bsize, uint32_t p,
+                                        uint32_t* __restrict__ boff) {
     __shared__ uint32_t buf[MAX_P + 1];
     __shared__ uint32_t scratch[32];
-    uint32_t mx = 0;
-    for (uint32_t b = threadIdx.x; b < p; b += blockDim.x) {
-        buf[b] = bsize[b];
-        mx = max(mx, bsize[b]);
-    }
-    atomicMax(maxb, mx);
+    for (uint32_t b = threadIdx.x; b < p; b += blockDim.x) buf[b] = bsize[b];
     const uint32_t total = block_exclusive_scan(buf, (int)p, scratch);
     for (uint32_t b = threadIdx.x; b < p; b += blockDim.x) boff[b] = buf[b];
     if (threadIdx.x == 0) boff[p] = total;
