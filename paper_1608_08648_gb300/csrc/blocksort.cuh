@@ -1,10 +1,11 @@
 // Stable block-wide merge sort in registers and shared memory (the bucket
-// sort of step 5).  NT threads each own IT consecutive keys: they sort them in
-// registers with an odd-even transposition network (adjacent compare-exchange
-// on strict '>', hence stable), then log2(NT) rounds merge pairs of sorted
-// runs.  Each round every thread finds where its IT outputs start with a
-// merge-path binary search over the two runs in shared memory and merges them
-// serially, taking from the left run on ties (stable).
+// sort of step 5).  NT threads each own IT consecutive keys and sort them in
+// registers: with a payload by an odd-even transposition network (adjacent
+// compare-exchange on strict '>', hence stable); keys only by Batcher's
+// odd-even merge sort network (equal keys are indistinguishable there).  Then
+// log2(NT) rounds merge pairs of sorted runs: every thread finds where its IT
+// outputs start with a merge-path binary search over the two runs in shared
+// memory and merges them serially, taking from the left run on ties (stable).
 #pragma once
 
 #include "common.cuh"
@@ -37,16 +38,37 @@ __device__ void block_merge_sort(O* sk, uint32_t* sv, int total) {
             k[i] = sk[pad_idx<O>(tid * IT + i)];
             if (HV) v[i] = sv[pad_idx<uint32_t>(tid * IT + i)];
         }
-        // Odd-even transposition sort of the IT keys (stable).
+        if (HV) {
+            // Odd-even transposition sort of the IT keys: adjacent compare-exchange
+            // on strict '>' keeps equal keys in order (stable, so payloads follow
+            // the stable order).
 #pragma unroll
-        for (int r = 0; r < IT; ++r) {
+            for (int r = 0; r < IT; ++r) {
 #pragma unroll
-            for (int j = r & 1; j + 1 < IT; j += 2) {
-                if (k[j + 1] < k[j]) {
-                    O t = k[j]; k[j] = k[j + 1]; k[j + 1] = t;
-                    if (HV) { uint32_t w = v[j]; v[j] = v[j + 1]; v[j + 1] = w; }
+                for (int j = r & 1; j + 1 < IT; j += 2) {
+                    if (k[j + 1] < k[j]) {
+                        O t = k[j]; k[j] = k[j + 1]; k[j + 1] = t;
+                        uint32_t w = v[j]; v[j] = v[j + 1]; v[j + 1] = w;
+                    }
                 }
             }
+        } else {
+            // Keys only: equal keys are identical bit patterns, so any sorting
+            // network will do; Batcher's odd-even merge sort (63 compare-exchanges
+            // for 16 keys, 19 for 8), branch-free with min / max.
+#pragma unroll
+            for (int pp = 1; pp < IT; pp <<= 1)
+#pragma unroll
+                for (int kk = pp; kk >= 1; kk >>= 1)
+#pragma unroll
+                    for (int j = kk % pp; j + kk < IT; j += 2 * kk)
+#pragma unroll
+                        for (int i = 0; i < kk; ++i)
+                            if (i + j + kk < IT && (i + j) / (2 * pp) == (i + j + kk) / (2 * pp)) {
+                                const O a = k[i + j], b = k[i + j + kk];
+                                k[i + j] = a < b ? a : b;
+                                k[i + j + kk] = a < b ? b : a;
+                            }
         }
     }
     for (int run = IT; run < total; run *= 2) {
@@ -79,21 +101,22 @@ __device__ void block_merge_sort(O* sk, uint32_t* sv, int total) {
                 va = sv[pad_idx<uint32_t>(A + min(ai, run - 1))];
                 vb = sv[pad_idx<uint32_t>(B + min(bi, run - 1))];
             }
+            // Branch-free serial merge: one shared-memory read per output.
 #pragma unroll
             for (int i = 0; i < IT; ++i) {
                 const bool takeA = (bi >= run) || (ai < run && ka <= kb);
                 k[i] = takeA ? ka : kb;
                 if (HV) v[i] = takeA ? va : vb;
-                if (takeA) {
-                    ++ai;
-                    const int q = A + min(ai, run - 1);
-                    ka = sk[pad_idx<O>(q)];
-                    if (HV) va = sv[pad_idx<uint32_t>(q)];
-                } else {
-                    ++bi;
-                    const int q = B + min(bi, run - 1);
-                    kb = sk[pad_idx<O>(q)];
-                    if (HV) vb = sv[pad_idx<uint32_t>(q)];
+                ai += takeA ? 1 : 0;
+                bi += takeA ? 0 : 1;
+                const int q = takeA ? A + min(ai, run - 1) : B + min(bi, run - 1);
+                const O nk = sk[pad_idx<O>(q)];
+                ka = takeA ? nk : ka;
+                kb = takeA ? kb : nk;
+                if (HV) {
+                    const uint32_t nv = sv[pad_idx<uint32_t>(q)];
+                    va = takeA ? nv : va;
+                    vb = takeA ? vb : nv;
                 }
             }
         }

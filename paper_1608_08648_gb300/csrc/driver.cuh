@@ -84,11 +84,11 @@ void segment_sort(Ctx& c, SegSpec ss, const typename KT::T* src, const uint32_t*
         wl.part[1] = c.ar.take<WorkItem>(wl.part_cap);
     }
     if (!c.live()) return;
-    cudaFuncSetAttribute(k_leaf<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::leaf_bytes);
-    const uint32_t grid_l = (uint32_t)(c.num_sms * occupancy(k_leaf<KT, HV>, BK_NT, L::leaf_bytes));
+    cudaFuncSetAttribute(k_leaf<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LeafSmem<KT, HV>::bytes);
+    const uint32_t grid_l = (uint32_t)(c.num_sms * occupancy(k_leaf<KT, HV>, BK_NT, LeafSmem<KT, HV>::bytes));
     if (direct) {
         OS_LAUNCH(c.st, c.nested ? "k_leaf.sample" : "k_leaf",
-                  k_leaf<KT, HV><<<std::min(ss.nseg, grid_l), BK_NT, L::leaf_bytes, c.st>>>(true, ss, bufs, wl, c.status));
+                  k_leaf<KT, HV><<<std::min(ss.nseg, grid_l), BK_NT, LeafSmem<KT, HV>::bytes, c.st>>>(true, ss, bufs, wl, c.status));
         return;
     }
     os_memset_async(wl.counts, 0, sizeof(uint32_t) * (MAX_DEPTH + 1), c.st);
@@ -100,7 +100,7 @@ void segment_sort(Ctx& c, SegSpec ss, const typename KT::T* src, const uint32_t*
                   k_repart<KT, HV><<<g, BK_NT, L::bytes, c.st>>>(level, ss, bufs, wl, seed, c.status, c.status + 1,
                                                                  reinterpret_cast<unsigned long long*>(c.status + 4)));
     }
-    OS_LAUNCH(c.st, c.nested ? "k_leaf.sample" : "k_leaf", k_leaf<KT, HV><<<grid_l, BK_NT, L::leaf_bytes, c.st>>>(false, ss, bufs, wl, c.status));
+    OS_LAUNCH(c.st, c.nested ? "k_leaf.sample" : "k_leaf", k_leaf<KT, HV><<<grid_l, BK_NT, LeafSmem<KT, HV>::bytes, c.st>>>(false, ss, bufs, wl, c.status));
 }
 
 template <class KT>

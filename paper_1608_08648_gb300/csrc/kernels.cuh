@@ -10,6 +10,7 @@
 //   step 5 (sort every bucket)          k_repart + k_leaf over the p buckets
 #pragma once
 
+#include "bitonic.cuh"
 #include "blocksort.cuh"
 #include "common.cuh"
 
@@ -36,6 +37,22 @@ template <> struct Tree<uint32_t> {
         for (int d = 0; d < h; ++d) v = 2 * v + (x > c[v] ? 1 : 0);
         return v - (1 << h);
     }
+    // N searches advanced level by level, so their shared-memory loads overlap.
+    // Key i has tag t0 + i * dt.
+    template <int N>
+    __device__ __forceinline__ void find_n(const uint32_t (&o)[N], uint32_t t0, uint32_t dt, int h, int (&v)[N]) const {
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] = 1;
+        for (int d = 0; d < h; ++d) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const uint64_t x = ((uint64_t)o[i] << 32) | (t0 + i * dt);
+                v[i] = 2 * v[i] + (x > c[v[i]] ? 1 : 0);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] -= 1 << h;
+    }
 };
 
 template <> struct Tree<uint64_t> {
@@ -55,6 +72,21 @@ template <> struct Tree<uint64_t> {
             v = 2 * v + (((o > so) | ((o == so) & (t > t_[v]))) ? 1 : 0);
         }
         return v - (1 << h);
+    }
+    template <int N>
+    __device__ __forceinline__ void find_n(const uint64_t (&o)[N], uint32_t t0, uint32_t dt, int h, int (&v)[N]) const {
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] = 1;
+        for (int d = 0; d < h; ++d) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const uint64_t so = o_[v[i]];
+                const uint32_t t = t0 + i * dt;
+                v[i] = 2 * v[i] + (((o[i] > so) | ((o[i] == so) & (t > t_[v[i]]))) ? 1 : 0);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] -= 1 << h;
     }
 };
 
@@ -189,7 +221,7 @@ __host__ __device__ inline uint32_t tile_lo(uint32_t g, uint32_t G, uint32_t nti
 }
 
 template <class KT>
-__global__ void __launch_bounds__(TOP_NT)
+__global__ void __launch_bounds__(TOP_NT, 3)
 k_classify(const typename KT::T* __restrict__ keys, uint32_t n, const typename KT::O* __restrict__ spl_o,
            const uint32_t* __restrict__ spl_t, int p, int h, uint32_t* __restrict__ hist, uint32_t ntiles) {
     using O = typename KT::O;
@@ -207,18 +239,20 @@ k_classify(const typename KT::T* __restrict__ keys, uint32_t n, const typename K
     for (uint32_t t = t0; t < t1; ++t) {
         const uint32_t base = t * TOP_TILE + w * (TOP_IT * 32) + lane;
         O o[TOP_IT];
+        int bk[TOP_IT];
 #pragma unroll
         for (int i = 0; i < TOP_IT; ++i) {
             const uint32_t e = base + i * 32;
             o[i] = e < n ? KT::ord(keys[e]) : O(0);
         }
+        tr.template find_n<TOP_IT>(o, base, 32, h, bk);
 #pragma unroll
         for (int i = 0; i < TOP_IT; ++i) {
             const uint32_t e = base + i * 32;
             const bool valid = e < n;
             const unsigned act = __ballot_sync(0xffffffffu, valid);
             if (valid) {
-                const int b = tr.find(o[i], e, h);
+                const int b = bk[i];
                 const unsigned m = __match_any_sync(act, b);
                 if (lane == __ffs(m) - 1) atomicAdd(&cnt[b], __popc(m));
             }
@@ -273,7 +307,7 @@ static __global__ void k_bucket_offsets(const uint32_t* __restrict__ bsize, uint
 // shared memory grouped by bucket and written out as contiguous runs.
 // ---------------------------------------------------------------------------
 template <class KT, bool HV>
-__global__ void __launch_bounds__(TOP_NT)
+__global__ void __launch_bounds__(TOP_NT, 3)
 k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ vals, uint32_t n,
           const typename KT::O* __restrict__ spl_o, const uint32_t* __restrict__ spl_t, int p, int h,
           const uint32_t* __restrict__ col, const uint32_t* __restrict__ boff, typename KT::T* __restrict__ out,
@@ -306,6 +340,7 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
         const uint32_t base = tbase + w * (TOP_IT * 32) + lane;
         T kv[TOP_IT];
         uint32_t br[TOP_IT];   // bucket << 16 | rank inside the warp
+        int bk[TOP_IT];
 #pragma unroll
         for (int i = 0; i < TOP_IT; ++i) {
             const uint32_t e = base + i * 32;
@@ -313,11 +348,17 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
         }
         for (int b = lane; b <= p; b += 32) mycnt[b] = 0;
         __syncthreads();   // tree/cursors ready; previous tile fully written out
+        {
+            O o[TOP_IT];
+#pragma unroll
+            for (int i = 0; i < TOP_IT; ++i) o[i] = KT::ord(kv[i]);
+            tr.template find_n<TOP_IT>(o, base, 32, h, bk);
+        }
 #pragma unroll
         for (int i = 0; i < TOP_IT; ++i) {
             const uint32_t e = base + i * 32;
             const bool valid = e < n;
-            const int b = valid ? tr.find(KT::ord(kv[i]), e, h) : p;
+            const int b = valid ? bk[i] : p;
             const unsigned m = __match_any_sync(0xffffffffu, b);
             const uint32_t c0 = mycnt[b];
             br[i] = ((uint32_t)b << 16) | (c0 + __popc(m & lanemask_lt()));
@@ -416,23 +457,55 @@ struct BucketSmem {
     static constexpr size_t cnt_bytes = al16(sizeof(uint16_t) * BK_WARPS * (MAXP2 + 1));
     static constexpr size_t small_bytes = sizeof(uint32_t) * (4 * (MAXP2 + 1) + 32);
     static constexpr size_t bytes = sk_bytes + sv_bytes + sb_bytes + tree_bytes + cnt_bytes + small_bytes + 64;
-    static constexpr size_t leaf_bytes = sk_bytes + sv_bytes;
 };
 
+// Shared memory of one leaf sort: the exchange area of the bitonic network
+// (which also stages the keys) and, with a payload, the payloads in input order.
+template <class KT, bool HV>
+struct LeafSmem {
+    using O = typename KT::O;
+    using E = typename LeafElem<O, HV>::E;
+    static constexpr int IT = LeafIT<O>::v;
+    static constexpr int CAP = Cap<O>::v;
+    static constexpr size_t ex_bytes = (sizeof(E) * padded_len<E>(CAP) + 15) & ~size_t(15);
+    static constexpr size_t bytes = ex_bytes + (HV ? sizeof(uint32_t) * CAP : 0);
+};
+
+// Sort [beg, beg+len) of `in` (len <= CAP) into the same range of `out`.
 template <class KT, bool HV>
 __device__ void leaf_sort(const typename KT::T* in, const uint32_t* vin, typename KT::T* out, uint32_t* vout,
-                          uint32_t beg, uint32_t len, typename KT::O* sk, uint32_t* sv) {
+                          uint32_t beg, uint32_t len, char* smem) {
     using O = typename KT::O;
-    constexpr int IT = LeafIT<O>::v;
-    const int ext = sort_extent<IT>((int)len);
-    for (int j = threadIdx.x; j < ext; j += BK_NT) {
-        sk[pad_idx<O>(j)] = j < (int)len ? KT::ord(in[beg + j]) : OMax<O>::v;
-        if (HV) sv[pad_idx<uint32_t>(j)] = j < (int)len ? vin[beg + j] : 0u;
+    using LE = LeafElem<O, HV>;
+    using E = typename LE::E;
+    using LS = LeafSmem<KT, HV>;
+    constexpr int IT = LS::IT;
+    E* ex = reinterpret_cast<E*>(smem);
+    uint32_t* sv = reinterpret_cast<uint32_t*>(smem + LS::ex_bytes);
+    int total = sort_extent<IT>((int)len);
+    if (total < 32 * IT) total = 32 * IT;
+    for (int j = threadIdx.x; j < total; j += BK_NT) {
+        ex[pad_idx<E>(j)] = LE::make(j < (int)len ? KT::ord(in[beg + j]) : OMax<O>::v, (uint32_t)j);
+        if (HV && j < (int)len) sv[j] = vin[beg + j];
     }
-    block_merge_sort<O, HV, BK_NT, IT>(sk, sv, ext);
+    __syncthreads();
+    E x[IT];
+    const int base = threadIdx.x * IT;
+    if (base < total) {
+#pragma unroll
+        for (int i = 0; i < IT; ++i) x[i] = ex[pad_idx<E>(base + i)];
+    }
+    bitonic_block<E, BK_NT, IT>(x, ex, total);
+    __syncthreads();
+    if (base < total) {
+#pragma unroll
+        for (int i = 0; i < IT; ++i) ex[pad_idx<E>(base + i)] = x[i];
+    }
+    __syncthreads();
     for (int j = threadIdx.x; j < (int)len; j += BK_NT) {
-        out[beg + j] = KT::key(sk[pad_idx<O>(j)]);
-        if (HV) vout[beg + j] = sv[pad_idx<uint32_t>(j)];
+        const E y = ex[pad_idx<E>(j)];
+        out[beg + j] = KT::key(LE::key(y));
+        if (HV) vout[beg + j] = sv[LE::pos(y)];
     }
     __syncthreads();
 }
@@ -497,18 +570,20 @@ __device__ int cta_partition(const typename KT::T* in, const uint32_t* vin, type
     for (uint32_t tb = 0; tb < len; tb += TILE) {
         const uint32_t base = tb + w * (IT * 32) + lane;
         O o[IT];
+        int bk[IT];
 #pragma unroll
         for (int i = 0; i < IT; ++i) {
             const uint32_t e = base + i * 32;
             o[i] = e < len ? KT::ord(in[beg + e]) : O(0);
         }
+        tr.template find_n<IT>(o, base, 32, h, bk);
 #pragma unroll
         for (int i = 0; i < IT; ++i) {
             const uint32_t e = base + i * 32;
             const bool valid = e < len;
             const unsigned act = __ballot_sync(0xffffffffu, valid);
             if (valid) {
-                const int b = tr.find(o[i], e, h);
+                const int b = bk[i];
                 const unsigned m = __match_any_sync(act, b);
                 if (lane == __ffs(m) - 1) atomicAdd(&part[b], __popc(m));
             }
@@ -527,6 +602,7 @@ __device__ int cta_partition(const typename KT::T* in, const uint32_t* vin, type
         const uint32_t base = tb + w * (IT * 32) + lane;
         T kv[IT];
         uint32_t br[IT];   // bucket << 16 | rank inside the warp
+        int bk[IT];
 #pragma unroll
         for (int i = 0; i < IT; ++i) {
             const uint32_t e = base + i * 32;
@@ -534,11 +610,17 @@ __device__ int cta_partition(const typename KT::T* in, const uint32_t* vin, type
         }
         for (int b = lane; b <= p2; b += 32) mycnt[b] = 0;
         __syncthreads();
+        {
+            O o[IT];
+#pragma unroll
+            for (int i = 0; i < IT; ++i) o[i] = KT::ord(kv[i]);
+            tr.template find_n<IT>(o, base, 32, h, bk);
+        }
 #pragma unroll
         for (int i = 0; i < IT; ++i) {
             const uint32_t e = base + i * 32;
             const bool valid = e < len;
-            const int b = valid ? tr.find(KT::ord(kv[i]), e, h) : p2;
+            const int b = valid ? bk[i] : p2;
             const unsigned m = __match_any_sync(0xffffffffu, b);
             const uint32_t c0 = mycnt[b];
             br[i] = ((uint32_t)b << 16) | (c0 + __popc(m & lanemask_lt()));
@@ -676,14 +758,15 @@ k_repart(int level, SegSpec ss, SortBufs<KT> bufs, WorkLists wl, uint64_t seed, 
 
 // Shared-memory sort of every leaf: the segments of ss directly (direct = true)
 // or the leaf list.  Persistent: CTAs stride over the work.
+// Resident leaf CTAs per SM the register budget is sized for: two, except for
+// 64-bit keys with a payload, whose (key, position) elements need more registers.
+template <class KT, bool HV> struct LeafOcc { static constexpr int v = (sizeof(typename KT::O) == 8 && HV) ? 1 : 2; };
+
 template <class KT, bool HV>
-__global__ void __launch_bounds__(BK_NT, 2)
+__global__ void __launch_bounds__(BK_NT, LeafOcc<KT, HV>::v)
 k_leaf(bool direct, SegSpec ss, SortBufs<KT> bufs, WorkLists wl, uint32_t* status) {
-    using O = typename KT::O;
     using L = BucketSmem<KT, HV>;
     extern __shared__ __align__(16) char smem[];
-    O* sk = reinterpret_cast<O*>(smem);
-    uint32_t* sv = reinterpret_cast<uint32_t*>(smem + L::sk_bytes);
     const uint32_t nwork = direct ? ss.nseg : min(wl.counts[0], wl.leaf_cap);
     for (uint32_t it = blockIdx.x; it < nwork; it += gridDim.x) {
         uint32_t beg, len, buf;
@@ -701,7 +784,7 @@ k_leaf(bool direct, SegSpec ss, SortBufs<KT> bufs, WorkLists wl, uint32_t* statu
             if (threadIdx.x == 0) flag_bounds(status, 6, (uint64_t)beg + len);
             continue;
         }
-        leaf_sort<KT, HV>(bufs.key_buf(buf), bufs.val_buf(buf), bufs.out, bufs.vout, beg, len, sk, sv);
+        leaf_sort<KT, HV>(bufs.key_buf(buf), bufs.val_buf(buf), bufs.out, bufs.vout, beg, len, smem);
     }
 }
 
