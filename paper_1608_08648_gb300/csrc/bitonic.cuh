@@ -142,4 +142,41 @@ __device__ void bitonic_block(E (&x)[IT], E* ex, int total) {
     }
 }
 
+// Bitonic sort of G = 16 * GIT elements held by a 16-lane group (lane l of the
+// group owns elements l*GIT .. l*GIT+GIT-1 in registers).  Only the stages of a
+// network over `ext` elements run (ext: a power of two, warp-uniform, at most
+// G; elements at or beyond ext must be the maximum).  Both 16-lane groups of a
+// warp execute the same stages.  Keys only (E32 / E64): ascending.
+template <class E, int GIT>
+__device__ __forceinline__ void bitonic_group16(E (&x)[GIT], int ext) {
+    constexpr int LOG_GIT = GIT == 8 ? 3 : GIT == 16 ? 4 : 5;
+    static_assert((1 << LOG_GIT) == GIT, "GIT must be 8, 16 or 32");
+    constexpr int LOG_G = LOG_GIT + 4;
+    const int gl = threadIdx.x & 15;          // lane inside the group
+    const int base = gl * GIT;
+#pragma unroll
+    for (int lk = 1; lk <= LOG_G; ++lk) {
+        const int kk = 1 << lk;
+        if (kk > ext) continue;
+#pragma unroll
+        for (int lj = lk - 1; lj >= 0; --lj) {
+            const int jj = 1 << lj;
+            if (jj < GIT) {
+#pragma unroll
+                for (int i = 0; i < GIT; ++i) {
+                    if ((i & jj) == 0) {
+                        const bool up = ((base + i) & kk) == 0;
+                        cas_dir(x[i], x[i + jj], up);
+                    }
+                }
+            } else {
+                const int lm = jj / GIT;      // < 16: the partner stays inside the group
+                const bool keep_min = ((base & jj) == 0) == ((base & kk) == 0);
+#pragma unroll
+                for (int i = 0; i < GIT; ++i) x[i] = keep(x[i], E::shfl(x[i], lm), keep_min);
+            }
+        }
+    }
+}
+
 }  // namespace ossort

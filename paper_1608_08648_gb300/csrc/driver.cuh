@@ -84,11 +84,12 @@ void segment_sort(Ctx& c, SegSpec ss, const typename KT::T* src, const uint32_t*
         wl.part[1] = c.ar.take<WorkItem>(wl.part_cap);
     }
     if (!c.live()) return;
-    cudaFuncSetAttribute(k_leaf<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LeafSmem<KT, HV>::bytes);
-    const uint32_t grid_l = (uint32_t)(c.num_sms * occupancy(k_leaf<KT, HV>, BK_NT, LeafSmem<KT, HV>::bytes));
+    const size_t leaf_smem = HV ? LeafSmem<KT, HV>::bytes : PartLeafSmem<KT>::bytes;
+    cudaFuncSetAttribute(k_leaf<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf_smem);
+    const uint32_t grid_l = (uint32_t)(c.num_sms * occupancy(k_leaf<KT, HV>, BK_NT, leaf_smem));
     if (direct) {
         OS_LAUNCH(c.st, c.nested ? "k_leaf.sample" : "k_leaf",
-                  k_leaf<KT, HV><<<std::min(ss.nseg, grid_l), BK_NT, LeafSmem<KT, HV>::bytes, c.st>>>(true, ss, bufs, wl, c.status));
+                  k_leaf<KT, HV><<<std::min(ss.nseg, grid_l), BK_NT, leaf_smem, c.st>>>(true, ss, bufs, wl, seed, c.status));
         return;
     }
     os_memset_async(wl.counts, 0, sizeof(uint32_t) * (MAX_DEPTH + 1), c.st);
@@ -100,7 +101,7 @@ void segment_sort(Ctx& c, SegSpec ss, const typename KT::T* src, const uint32_t*
                   k_repart<KT, HV><<<g, BK_NT, L::bytes, c.st>>>(level, ss, bufs, wl, seed, c.status, c.status + 1,
                                                                  reinterpret_cast<unsigned long long*>(c.status + 4)));
     }
-    OS_LAUNCH(c.st, c.nested ? "k_leaf.sample" : "k_leaf", k_leaf<KT, HV><<<grid_l, BK_NT, LeafSmem<KT, HV>::bytes, c.st>>>(false, ss, bufs, wl, c.status));
+    OS_LAUNCH(c.st, c.nested ? "k_leaf.sample" : "k_leaf", k_leaf<KT, HV><<<grid_l, BK_NT, leaf_smem, c.st>>>(false, ss, bufs, wl, seed, c.status));
 }
 
 template <class KT>
@@ -109,12 +110,11 @@ size_t classify_smem(int p, int P) {
 }
 
 template <class KT, bool HV>
-size_t scatter_smem(int p, int P) {
+size_t scatter_smem(int p) {
     using T = typename KT::T;
-    size_t b = ((size_t)Tree<typename KT::O>::node_bytes * P + 15) & ~size_t(15);
-    b += sizeof(T) * TOP_TILE + (HV ? sizeof(uint32_t) * TOP_TILE : 0);
+    size_t b = sizeof(T) * TOP_TILE + (HV ? sizeof(uint32_t) * TOP_TILE : 0);
     b += sizeof(uint32_t) * (p + 1) + sizeof(uint32_t) * p + sizeof(uint32_t) * 32;
-    b += sizeof(uint16_t) * TOP_TILE + sizeof(uint16_t) * TOP_WARPS * (p + 1);
+    b += sizeof(uint16_t) * TOP_TILE + (HV ? sizeof(uint16_t) * TOP_WARPS * (p + 1) : 0);
     return b;
 }
 
@@ -131,20 +131,21 @@ void partition_top(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, uint
     const uint32_t gmax = std::min<uint32_t>(std::max<uint32_t>(ntiles, 1), G_CAP);
     uint32_t* hist = c.ar.take<uint32_t>((size_t)p * gmax);
     uint32_t* col = c.ar.take<uint32_t>((size_t)p * gmax);
+    uint16_t* bid = c.ar.take<uint16_t>(n);
     if (!c.live()) return;
-    const size_t sm_c = classify_smem<KT>(p, P), sm_s = scatter_smem<KT, HV>(p, P);
+    const size_t sm_c = classify_smem<KT>(p, P), sm_s = scatter_smem<KT, HV>(p);
     cudaFuncSetAttribute(k_classify<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c);
     cudaFuncSetAttribute(k_scatter<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_s);
     const int occ = occupancy(k_scatter<KT, HV>, TOP_NT, sm_s);
     const uint32_t G = std::max<uint32_t>(1, std::min<uint32_t>(gmax, (uint32_t)(c.num_sms * occ)));
     OS_LAUNCH(c.st, c.nested ? "k_classify.sample" : "k_classify",
-              k_classify<KT><<<G, TOP_NT, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, h, hist, ntiles));
+              k_classify<KT><<<G, TOP_NT, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, h, hist, bid, ntiles));
     OS_LAUNCH(c.st, c.nested ? "k_column_scan.sample" : "k_column_scan",
               k_column_scan<<<grid_for((uint64_t)p * 32, 256), 256, 0, c.st>>>(hist, p, G, col, bsize));
     OS_LAUNCH(c.st, c.nested ? "k_bucket_offsets.sample" : "k_bucket_offsets", k_bucket_offsets<<<1, 1024, 0, c.st>>>(bsize, p, boff));
     OS_LAUNCH(c.st, c.nested ? "k_scatter.sample" : "k_scatter",
-              k_scatter<KT, HV><<<G, TOP_NT, sm_s, c.st>>>(src, vsrc, n, spl_o, spl_t, (int)p, h, col, boff, dst,
-                                                           vdst, ntiles, c.status));
+              k_scatter<KT, HV><<<G, TOP_NT, sm_s, c.st>>>(src, vsrc, bid, n, (int)p, col, boff, dst, vdst,
+                                                           ntiles, c.status));
 }
 
 template <class KT, bool HV>

@@ -213,8 +213,9 @@ __global__ void k_pick_splitters(const typename KT::T* __restrict__ tk, const ui
 
 // ---------------------------------------------------------------------------
 // Step 4, pass 1: every CTA owns a contiguous run of tiles, finds the bucket of
-// each key (tag = its position in the array) and counts keys per bucket.
-// hist is bucket-major: hist[b * G + g].
+// each key (tag = its position in the array), stores it in bid (two bytes a
+// key, read back by the scatter instead of searching again) and counts keys
+// per bucket.  hist is bucket-major: hist[b * G + g].
 // ---------------------------------------------------------------------------
 __host__ __device__ inline uint32_t tile_lo(uint32_t g, uint32_t G, uint32_t ntiles) {
     return (uint32_t)(((uint64_t)g * ntiles) / G);
@@ -223,7 +224,8 @@ __host__ __device__ inline uint32_t tile_lo(uint32_t g, uint32_t G, uint32_t nti
 template <class KT>
 __global__ void __launch_bounds__(TOP_NT, 3)
 k_classify(const typename KT::T* __restrict__ keys, uint32_t n, const typename KT::O* __restrict__ spl_o,
-           const uint32_t* __restrict__ spl_t, int p, int h, uint32_t* __restrict__ hist, uint32_t ntiles) {
+           const uint32_t* __restrict__ spl_t, int p, int h, uint32_t* __restrict__ hist, uint16_t* __restrict__ bid,
+           uint32_t ntiles) {
     using O = typename KT::O;
     extern __shared__ __align__(16) char smem[];
     const int P = 1 << h;
@@ -253,6 +255,7 @@ k_classify(const typename KT::T* __restrict__ keys, uint32_t n, const typename K
             const unsigned act = __ballot_sync(0xffffffffu, valid);
             if (valid) {
                 const int b = bk[i];
+                bid[e] = (uint16_t)b;
                 const unsigned m = __match_any_sync(act, b);
                 if (lane == __ffs(m) - 1) atomicAdd(&cnt[b], __popc(m));
             }
@@ -299,37 +302,34 @@ static __global__ void k_bucket_offsets(const uint32_t* __restrict__ bsize, uint
 }
 
 // ---------------------------------------------------------------------------
-// Step 4, pass 2: the same CTAs walk the same tiles in order, find each key's
-// bucket again and move the keys (and payloads) into their buckets.  Inside a
-// tile a key's rank among the tile's keys of its bucket comes from per-warp
-// counters (__match_any_sync groups) plus a cross-warp prefix, so every bucket
-// receives its keys in input order (a stable scatter).  Keys are staged in
-// shared memory grouped by bucket and written out as contiguous runs.
+// Step 4, pass 2: the same CTAs walk the same tiles in order and move the keys
+// (and payloads) into their buckets, using the bucket ids of pass 1.  Keys are
+// staged in shared memory grouped by bucket and written out as contiguous runs.
+// With a payload the scatter is stable: a key's rank among the tile's keys of
+// its bucket comes from per-warp counters (__match_any_sync groups) plus a
+// cross-warp prefix, so every bucket receives its keys in input order.  Keys
+// alone need no order inside a bucket (equal keys are identical), so a
+// warp-aggregated shared-memory atomic hands out the slots.
 // ---------------------------------------------------------------------------
 template <class KT, bool HV>
 __global__ void __launch_bounds__(TOP_NT, 3)
-k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ vals, uint32_t n,
-          const typename KT::O* __restrict__ spl_o, const uint32_t* __restrict__ spl_t, int p, int h,
-          const uint32_t* __restrict__ col, const uint32_t* __restrict__ boff, typename KT::T* __restrict__ out,
-          uint32_t* __restrict__ vout, uint32_t ntiles, uint32_t* status) {
-    using O = typename KT::O;
+k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ vals,
+          const uint16_t* __restrict__ bid, uint32_t n, int p, const uint32_t* __restrict__ col,
+          const uint32_t* __restrict__ boff, typename KT::T* __restrict__ out, uint32_t* __restrict__ vout,
+          uint32_t ntiles, uint32_t* status) {
     using T = typename KT::T;
     extern __shared__ __align__(16) char smem[];
-    const int P = 1 << h;
-    Tree<O> tr;
-    tr.bind(smem, P);
-    char* q = smem + ((Tree<O>::node_bytes * P + 15) & ~15);
+    char* q = smem;
     T* sk = reinterpret_cast<T*>(q);                 q += sizeof(T) * TOP_TILE;
     uint32_t* sv = reinterpret_cast<uint32_t*>(q);    q += HV ? sizeof(uint32_t) * TOP_TILE : 0;
     uint32_t* tile_off = reinterpret_cast<uint32_t*>(q); q += sizeof(uint32_t) * (p + 1);
     uint32_t* cursor = reinterpret_cast<uint32_t*>(q);   q += sizeof(uint32_t) * p;
     uint32_t* scratch = reinterpret_cast<uint32_t*>(q);  q += sizeof(uint32_t) * 32;
     uint16_t* sb = reinterpret_cast<uint16_t*>(q);       q += sizeof(uint16_t) * TOP_TILE;
-    uint16_t* cnt = reinterpret_cast<uint16_t*>(q);      // [TOP_WARPS][p + 1]
+    uint16_t* cnt = reinterpret_cast<uint16_t*>(q);      // HV: [TOP_WARPS][p + 1]
     const int cstride = p + 1;
 
     const uint32_t G = gridDim.x, g = blockIdx.x;
-    tree_from_arrays<O>(tr, spl_o, spl_t, p, h);
     for (int b = threadIdx.x; b < p; b += TOP_NT) cursor[b] = boff[b] + col[(size_t)b * G + g];
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -339,44 +339,53 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
         const uint32_t tbase = t * TOP_TILE;
         const uint32_t base = tbase + w * (TOP_IT * 32) + lane;
         T kv[TOP_IT];
-        uint32_t br[TOP_IT];   // bucket << 16 | rank inside the warp
-        int bk[TOP_IT];
+        uint32_t br[TOP_IT];   // bucket << 16 | rank inside the tile's part of the bucket
 #pragma unroll
         for (int i = 0; i < TOP_IT; ++i) {
             const uint32_t e = base + i * 32;
             kv[i] = e < n ? keys[e] : T(0);
+            br[i] = e < n ? (uint32_t)bid[e] : (uint32_t)p;
         }
-        for (int b = lane; b <= p; b += 32) mycnt[b] = 0;
-        __syncthreads();   // tree/cursors ready; previous tile fully written out
-        {
-            O o[TOP_IT];
-#pragma unroll
-            for (int i = 0; i < TOP_IT; ++i) o[i] = KT::ord(kv[i]);
-            tr.template find_n<TOP_IT>(o, base, 32, h, bk);
+        if (HV) {
+            for (int b = lane; b <= p; b += 32) mycnt[b] = 0;
+        } else {
+            for (int b = threadIdx.x; b <= p; b += TOP_NT) tile_off[b] = 0;
         }
+        __syncthreads();   // counters cleared; previous tile fully written out
+        if (HV) {
 #pragma unroll
-        for (int i = 0; i < TOP_IT; ++i) {
-            const uint32_t e = base + i * 32;
-            const bool valid = e < n;
-            const int b = valid ? bk[i] : p;
-            const unsigned m = __match_any_sync(0xffffffffu, b);
-            const uint32_t c0 = mycnt[b];
-            br[i] = ((uint32_t)b << 16) | (c0 + __popc(m & lanemask_lt()));
-            __syncwarp();
-            if (lane == __ffs(m) - 1) mycnt[b] = (uint16_t)(c0 + __popc(m));
-            __syncwarp();
-        }
-        __syncthreads();
-        // Cross-warp exclusive prefix per bucket; tile totals into tile_off.
-        for (int b = threadIdx.x; b < p; b += TOP_NT) {
-            uint32_t run = 0;
-#pragma unroll
-            for (int ww = 0; ww < TOP_WARPS; ++ww) {
-                const uint32_t c = cnt[ww * cstride + b];
-                cnt[ww * cstride + b] = (uint16_t)run;
-                run += c;
+            for (int i = 0; i < TOP_IT; ++i) {
+                const int b = (int)br[i];
+                const unsigned m = __match_any_sync(0xffffffffu, b);
+                const uint32_t c0 = mycnt[b];
+                br[i] = ((uint32_t)b << 16) | (c0 + __popc(m & lanemask_lt()));
+                __syncwarp();
+                if (lane == __ffs(m) - 1) mycnt[b] = (uint16_t)(c0 + __popc(m));
+                __syncwarp();
             }
-            tile_off[b] = run;
+            __syncthreads();
+            // Cross-warp exclusive prefix per bucket; tile totals into tile_off.
+            for (int b = threadIdx.x; b < p; b += TOP_NT) {
+                uint32_t run = 0;
+#pragma unroll
+                for (int ww = 0; ww < TOP_WARPS; ++ww) {
+                    const uint32_t c = cnt[ww * cstride + b];
+                    cnt[ww * cstride + b] = (uint16_t)run;
+                    run += c;
+                }
+                tile_off[b] = run;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < TOP_IT; ++i) {
+                const int b = (int)br[i];
+                const unsigned m = __match_any_sync(0xffffffffu, b);
+                const int leader = __ffs(m) - 1;
+                uint32_t c0 = 0;
+                if (lane == leader) c0 = atomicAdd(&tile_off[b], (uint32_t)__popc(m));
+                c0 = __shfl_sync(0xffffffffu, c0, leader);
+                br[i] = ((uint32_t)b << 16) | (c0 + __popc(m & lanemask_lt()));
+            }
         }
         const uint32_t tvalid = block_exclusive_scan(tile_off, p, scratch);
         if (threadIdx.x == 0) tile_off[p] = tvalid;
@@ -385,7 +394,7 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
         for (int i = 0; i < TOP_IT; ++i) {
             const int b = (int)(br[i] >> 16);
             if (b < p) {
-                const uint32_t loc = tile_off[b] + mycnt[b] + (br[i] & 0xFFFFu);
+                const uint32_t loc = tile_off[b] + (HV ? mycnt[b] : 0u) + (br[i] & 0xFFFFu);
                 if (loc >= (uint32_t)TOP_TILE) {
                     flag_bounds(status, 8, loc);
                     continue;
@@ -408,6 +417,7 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
         }
         __syncthreads();
         for (int b = threadIdx.x; b < p; b += TOP_NT) cursor[b] += tile_off[b + 1] - tile_off[b];
+        __syncthreads();   // tile_off is cleared at the top of the next tile
     }
 }
 
@@ -510,6 +520,171 @@ __device__ void leaf_sort(const typename KT::T* in, const uint32_t* vin, typenam
     __syncthreads();
 }
 
+// Keys-only leaf sort with one sample-sort level inside shared memory: a
+// stratified sample of the segment gives p3 - 1 tagged splitters (p3 <= 64), every
+// key is classified from registers and dropped into its sub-bucket of the
+// staging buffer (slots from warp-aggregated atomics: order inside a sub-bucket
+// is free for keys alone), the 32 16-lane groups then sort the sub-buckets (two
+// each) with the register bitonic network, and the finished segment is copied
+// out coalesced.  A segment whose largest sub-bucket exceeds a group's capacity
+// (rare) falls back to the block-wide bitonic sort.
+template <class O> struct PartLeaf {
+    static constexpr int LIT = LeafIT<O>::v;            // keys per thread while classifying
+    static constexpr int GIT = LeafIT<O>::v;            // keys per lane of a group sort
+    static constexpr int GCAP = 16 * GIT;               // keys one 16-lane group sorts
+    static constexpr int GROUPS = BK_NT / 16;
+    static constexpr int MAXP3 = 2 * GROUPS;            // sub-buckets (two per group)
+    static constexpr int SAMPLE3 = 1024;
+};
+
+template <class KT>
+struct PartLeafSmem {
+    using O = typename KT::O;
+    using PL = PartLeaf<O>;
+    static constexpr size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+    static constexpr size_t b_bytes = al16(sizeof(O) * padded_len<O>(Cap<O>::v));
+    static constexpr size_t sv_bytes = al16(sizeof(uint32_t) * padded_len<uint32_t>(PL::SAMPLE3));
+    static constexpr size_t tree_bytes = al16(Tree<O>::node_bytes * PL::MAXP3);
+    static constexpr size_t small_bytes = sizeof(uint32_t) * (2 * (PL::MAXP3 + 1) + 32 + 4);
+    static constexpr size_t own = b_bytes + sv_bytes + tree_bytes + small_bytes;
+    static constexpr size_t bytes = own > LeafSmem<KT, false>::bytes ? own : LeafSmem<KT, false>::bytes;
+};
+
+template <class KT>
+__device__ void part_leaf_sort(const typename KT::T* in, typename KT::T* out, uint32_t beg, uint32_t len,
+                               char* smem, uint64_t seed) {
+    using O = typename KT::O;
+    using PL = PartLeaf<O>;
+    using PS = PartLeafSmem<KT>;
+    using LE = LeafElem<O, false>;
+    using E = typename LE::E;
+    constexpr int LIT = PL::LIT, GIT = PL::GIT, GCAP = PL::GCAP, MAXP3 = PL::MAXP3;
+    char* q = smem;
+    O* B = reinterpret_cast<O*>(q);                 q += PS::b_bytes;
+    uint32_t* sv = reinterpret_cast<uint32_t*>(q);  q += PS::sv_bytes;
+    Tree<O> tr;
+    tr.bind(q, MAXP3);                               q += PS::tree_bytes;
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(q); q += sizeof(uint32_t) * (MAXP3 + 1);
+    uint32_t* scratch = reinterpret_cast<uint32_t*>(q + sizeof(uint32_t) * (MAXP3 + 1));
+    uint32_t* flag = scratch + 32;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int grp = tid >> 4, gl = tid & 15;
+
+    if (len <= (uint32_t)GCAP) {
+        // One group sorts the whole segment straight from global memory.
+        if (w == 0) {
+            E x[GIT];
+            int ext = 1;
+            while (ext < (int)len) ext <<= 1;
+#pragma unroll
+            for (int i = 0; i < GIT; ++i) {
+                const int e = gl * GIT + i;
+                x[i] = E{(grp == 0 && e < (int)len) ? KT::ord(in[beg + e]) : OMax<O>::v};
+            }
+            bitonic_group16<E, GIT>(x, ext);
+            if (grp == 0) {
+#pragma unroll
+                for (int i = 0; i < GIT; ++i) {
+                    const int e = gl * GIT + i;
+                    if (e < (int)len) out[beg + e] = KT::key(LE::key(x[i]));
+                }
+            }
+        }
+        __syncthreads();
+        return;
+    }
+
+    // 1. Splitters from a stratified sample tagged with positions.
+    int p3 = 2;
+    while (p3 < MAXP3 && (uint32_t)p3 * (GCAP / 2) < len) p3 <<= 1;   // mean sub-bucket <= GCAP/2
+    const int h3 = 31 - __clz(p3);
+    int m3 = PL::SAMPLE3;
+    while ((uint32_t)m3 > len) m3 >>= 1;
+    const uint64_t state = sm_stream(seed ^ ((uint64_t)beg * SM_GAMMA), 11);
+    for (int j = tid; j < m3; j += BK_NT) {
+        const uint32_t lo = (uint32_t)((uint64_t)j * len / m3);
+        const uint32_t hi = (uint32_t)((uint64_t)(j + 1) * len / m3);
+        const uint32_t pos = lo + (uint32_t)(sm_at(state, j) % (uint64_t)max(hi - lo, 1u));
+        B[pad_idx<O>(j)] = KT::ord(in[beg + pos]);
+        sv[pad_idx<uint32_t>(j)] = pos;
+    }
+    block_merge_sort<O, true, BK_NT, 2>(B, sv, m3);
+    const int stride = m3 / p3;
+    for (int v = tid + 1; v < p3; v += BK_NT) {
+        const int i = eytz_rank(v, h3);
+        tr.set(v, B[pad_idx<O>(i * stride - 1)], sv[pad_idx<uint32_t>(i * stride - 1)]);
+    }
+    for (int b = tid; b <= p3; b += BK_NT) cnt[b] = 0;
+    if (tid == 0) *flag = 0;
+    __syncthreads();
+
+    // 2. Classify from registers; warp-aggregated atomic slots.
+    const uint32_t base = w * (LIT * 32) + lane;
+    O o[LIT];
+    uint32_t bs[LIT];   // sub-bucket << 16 | slot
+    {
+        int bk[LIT];
+#pragma unroll
+        for (int i = 0; i < LIT; ++i) {
+            const uint32_t e = base + i * 32;
+            o[i] = e < len ? KT::ord(in[beg + e]) : O(0);
+        }
+        tr.template find_n<LIT>(o, base, 32, h3, bk);
+#pragma unroll
+        for (int i = 0; i < LIT; ++i) {
+            const uint32_t e = base + i * 32;
+            const int b = e < len ? bk[i] : p3;
+            const unsigned m = __match_any_sync(0xffffffffu, b);
+            const int leader = __ffs(m) - 1;
+            uint32_t c0 = 0;
+            if (lane == leader) c0 = atomicAdd(&cnt[b], (uint32_t)__popc(m));
+            c0 = __shfl_sync(0xffffffffu, c0, leader);
+            bs[i] = ((uint32_t)b << 16) | (c0 + __popc(m & lanemask_lt()));
+        }
+    }
+    const uint32_t total = block_exclusive_scan(cnt, p3, scratch);
+    if (tid == 0) cnt[p3] = total;
+    __syncthreads();
+    if (tid < p3 && cnt[tid + 1] - cnt[tid] > (uint32_t)GCAP) atomicOr(flag, 1u);
+    // 3. Drop every key into its sub-bucket.
+#pragma unroll
+    for (int i = 0; i < LIT; ++i) {
+        const int b = (int)(bs[i] >> 16);
+        if (b < p3) B[pad_idx<O>(cnt[b] + (bs[i] & 0xFFFFu))] = o[i];
+    }
+    __syncthreads();
+    if (*flag) {
+        leaf_sort<KT, false>(in, nullptr, out, nullptr, beg, len, smem);
+        return;
+    }
+    // 4. Every 16-lane group sorts its sub-buckets in registers, in place.
+#pragma unroll 1
+    for (int sb = grp; sb < PL::GROUPS * 2; sb += PL::GROUPS) {
+        const uint32_t gb = sb < p3 ? cnt[sb] : 0u;
+        const int gm = sb < p3 ? (int)(cnt[sb + 1] - gb) : 0;
+        int ext = 1;
+        while (ext < gm) ext <<= 1;
+        ext = (int)__reduce_max_sync(0xffffffffu, (unsigned)ext);
+        if (ext <= 1 && gm == 0) continue;   // warp-uniform: both groups of the warp are empty
+        E x[GIT];
+#pragma unroll
+        for (int i = 0; i < GIT; ++i) {
+            const int e = gl * GIT + i;
+            x[i] = E{e < gm ? B[pad_idx<O>(gb + e)] : OMax<O>::v};
+        }
+        bitonic_group16<E, GIT>(x, ext);
+#pragma unroll
+        for (int i = 0; i < GIT; ++i) {
+            const int e = gl * GIT + i;
+            if (e < gm) B[pad_idx<O>(gb + e)] = LE::key(x[i]);
+        }
+    }
+    __syncthreads();
+    // 5. The sub-buckets are in order: copy the segment out coalesced.
+    for (uint32_t j = tid; j < len; j += BK_NT) out[beg + j] = KT::key(B[pad_idx<O>(j)]);
+    __syncthreads();
+}
+
 // Repartition [beg, beg+len) of `in` into p2 children written to `outb`; child
 // offsets (relative to beg) go to off[0..p2].  Returns p2.
 template <class KT, bool HV>
@@ -595,20 +770,25 @@ __device__ int cta_partition(const typename KT::T* in, const uint32_t* vin, type
         cursor[b] = beg + part[b];
     }
     if (threadIdx.x == 0) off[p2] = total;
-    // 3. Stable scatter pass (same ranking scheme as k_scatter).
+    // 3. Scatter pass (ranking as in k_scatter: stable with a payload, atomic
+    //    slots for keys alone).
     const int cstride = MAXP2 + 1;
     uint16_t* mycnt = cnt + w * cstride;
     for (uint32_t tb = 0; tb < len; tb += TILE) {
         const uint32_t base = tb + w * (IT * 32) + lane;
         T kv[IT];
-        uint32_t br[IT];   // bucket << 16 | rank inside the warp
+        uint32_t br[IT];   // bucket << 16 | rank inside the tile's part of the child
         int bk[IT];
 #pragma unroll
         for (int i = 0; i < IT; ++i) {
             const uint32_t e = base + i * 32;
             kv[i] = e < len ? in[beg + e] : T(0);
         }
-        for (int b = lane; b <= p2; b += 32) mycnt[b] = 0;
+        if (HV) {
+            for (int b = lane; b <= p2; b += 32) mycnt[b] = 0;
+        } else {
+            for (int b = threadIdx.x; b <= p2; b += BK_NT) tile_off[b] = 0;
+        }
         __syncthreads();
         {
             O o[IT];
@@ -616,28 +796,42 @@ __device__ int cta_partition(const typename KT::T* in, const uint32_t* vin, type
             for (int i = 0; i < IT; ++i) o[i] = KT::ord(kv[i]);
             tr.template find_n<IT>(o, base, 32, h, bk);
         }
+        if (HV) {
 #pragma unroll
-        for (int i = 0; i < IT; ++i) {
-            const uint32_t e = base + i * 32;
-            const bool valid = e < len;
-            const int b = valid ? bk[i] : p2;
-            const unsigned m = __match_any_sync(0xffffffffu, b);
-            const uint32_t c0 = mycnt[b];
-            br[i] = ((uint32_t)b << 16) | (c0 + __popc(m & lanemask_lt()));
-            __syncwarp();
-            if (lane == __ffs(m) - 1) mycnt[b] = (uint16_t)(c0 + __popc(m));
-            __syncwarp();
-        }
-        __syncthreads();
-        for (int b = threadIdx.x; b < p2; b += BK_NT) {
-            uint32_t run = 0;
-#pragma unroll
-            for (int ww = 0; ww < BK_WARPS; ++ww) {
-                const uint32_t c = cnt[ww * cstride + b];
-                cnt[ww * cstride + b] = (uint16_t)run;
-                run += c;
+            for (int i = 0; i < IT; ++i) {
+                const uint32_t e = base + i * 32;
+                const bool valid = e < len;
+                const int b = valid ? bk[i] : p2;
+                const unsigned m = __match_any_sync(0xffffffffu, b);
+                const uint32_t c0 = mycnt[b];
+                br[i] = ((uint32_t)b << 16) | (c0 + __popc(m & lanemask_lt()));
+                __syncwarp();
+                if (lane == __ffs(m) - 1) mycnt[b] = (uint16_t)(c0 + __popc(m));
+                __syncwarp();
             }
-            tile_off[b] = run;
+            __syncthreads();
+            for (int b = threadIdx.x; b < p2; b += BK_NT) {
+                uint32_t run = 0;
+#pragma unroll
+                for (int ww = 0; ww < BK_WARPS; ++ww) {
+                    const uint32_t c = cnt[ww * cstride + b];
+                    cnt[ww * cstride + b] = (uint16_t)run;
+                    run += c;
+                }
+                tile_off[b] = run;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < IT; ++i) {
+                const uint32_t e = base + i * 32;
+                const int b = e < len ? bk[i] : p2;
+                const unsigned m = __match_any_sync(0xffffffffu, b);
+                const int leader = __ffs(m) - 1;
+                uint32_t c0 = 0;
+                if (lane == leader) c0 = atomicAdd(&tile_off[b], (uint32_t)__popc(m));
+                c0 = __shfl_sync(0xffffffffu, c0, leader);
+                br[i] = ((uint32_t)b << 16) | (c0 + __popc(m & lanemask_lt()));
+            }
         }
         const uint32_t tvalid = block_exclusive_scan(tile_off, p2, scratch);
         if (threadIdx.x == 0) tile_off[p2] = tvalid;
@@ -646,7 +840,7 @@ __device__ int cta_partition(const typename KT::T* in, const uint32_t* vin, type
         for (int i = 0; i < IT; ++i) {
             const int b = (int)(br[i] >> 16);
             if (b < p2) {
-                const uint32_t loc = tile_off[b] + mycnt[b] + (br[i] & 0xFFFFu);
+                const uint32_t loc = tile_off[b] + (HV ? mycnt[b] : 0u) + (br[i] & 0xFFFFu);
                 if (loc >= (uint32_t)TILE) {
                     flag_bounds(status, 9, loc);
                     continue;
@@ -669,8 +863,8 @@ __device__ int cta_partition(const typename KT::T* in, const uint32_t* vin, type
         }
         __syncthreads();
         for (int b = threadIdx.x; b < p2; b += BK_NT) cursor[b] += tile_off[b + 1] - tile_off[b];
+        __syncthreads();   // tile_off is cleared at the top of the next tile
     }
-    __syncthreads();
     return p2;
 }
 
@@ -764,7 +958,7 @@ template <class KT, bool HV> struct LeafOcc { static constexpr int v = (sizeof(t
 
 template <class KT, bool HV>
 __global__ void __launch_bounds__(BK_NT, LeafOcc<KT, HV>::v)
-k_leaf(bool direct, SegSpec ss, SortBufs<KT> bufs, WorkLists wl, uint32_t* status) {
+k_leaf(bool direct, SegSpec ss, SortBufs<KT> bufs, WorkLists wl, uint64_t seed, uint32_t* status) {
     using L = BucketSmem<KT, HV>;
     extern __shared__ __align__(16) char smem[];
     const uint32_t nwork = direct ? ss.nseg : min(wl.counts[0], wl.leaf_cap);
@@ -784,7 +978,8 @@ k_leaf(bool direct, SegSpec ss, SortBufs<KT> bufs, WorkLists wl, uint32_t* statu
             if (threadIdx.x == 0) flag_bounds(status, 6, (uint64_t)beg + len);
             continue;
         }
-        leaf_sort<KT, HV>(bufs.key_buf(buf), bufs.val_buf(buf), bufs.out, bufs.vout, beg, len, smem);
+        if (HV) leaf_sort<KT, HV>(bufs.key_buf(buf), bufs.val_buf(buf), bufs.out, bufs.vout, beg, len, smem);
+        else part_leaf_sort<KT>(bufs.key_buf(buf), bufs.out, beg, len, smem, seed);
     }
 }
 

@@ -75,8 +75,10 @@ def test_c1_det_int32_uniform_exact():
 def test_sizes_across_tiles(kt, split, n):
     keys = gen("uniform", n, kt, seed=n)
     check(keys, kt, split, 4, 2, seed=n)
+    check(keys, kt, split, 4, 2, seed=n, with_vals=False)
     if n >= 4097:
         check(keys, kt, split, 16, 3, seed=n + 1)
+        check(keys, kt, split, 16, 3, seed=n + 1, with_vals=False)
 
 
 @pytest.mark.parametrize("kt", ["i32", "u64", "f64"])
@@ -86,12 +88,14 @@ def test_distributions(kt, split, dist):
     n = (1 << 18) + 1234
     keys = gen(dist, n, kt, seed=3, p=64)
     check(keys, kt, split, 64, 8, seed=5)
+    check(keys, kt, split, 64, 8, seed=5, with_vals=False)
 
 
 @pytest.mark.parametrize("split", ["det", "ran"])
 def test_f64_special_values(split):
     keys = gen("edge", 200003, "f64", seed=11)
     check(keys, "f64", split, 32, 4, seed=7)
+    check(keys, "f64", split, 32, 4, seed=7, with_vals=False)
 
 
 @pytest.mark.parametrize("split", ["det", "ran"])
@@ -104,10 +108,11 @@ def test_u64_hot_keys_stable(split):
 def test_buckets_larger_than_a_cta(kt):
     """Few buckets: every bucket is repartitioned inside the bucket phase."""
     keys = gen("uniform", (1 << 21) + 5, kt, seed=9)
-    st = check(keys, kt, "ran", 4, 16, seed=9)
-    assert st["depth"] >= 1
-    st = check(keys, kt, "det", 8, 2, seed=9)
-    assert st["depth"] >= 1
+    for with_vals in (True, False):
+        st = check(keys, kt, "ran", 4, 16, seed=9, with_vals=with_vals)
+        assert st["depth"] >= 1
+        st = check(keys, kt, "det", 8, 2, seed=9, with_vals=with_vals)
+        assert st["depth"] >= 1
 
 
 def test_max_p_and_non_power_of_two_p():
@@ -124,6 +129,7 @@ def test_all_equal_keys_balance(split):
     keys = np.full(n, 42, dtype=np.int32)
     st = check(keys, "i32", split, 64, 8, seed=1)
     assert st["max_bucket"] <= 2 * n // 64 + 64
+    check(keys, "i32", split, 64, 8, seed=1, with_vals=False)
 
 
 @pytest.mark.parametrize("kt", ["i32", "f64"])
