@@ -80,12 +80,20 @@ constexpr int TOP_WARPS = TOP_NT / 32;
 constexpr int BK_NT = 512;           // threads of the bucket kernel
 constexpr int BK_WARPS = BK_NT / 32;
 constexpr int MAXP2 = 256;           // largest fan-out of an in-bucket repartition
+constexpr int MAXP2_LBITS = 9;       // bins of its splitter table: 2 * MAXP2
 constexpr int MAX_DEPTH = 4;         // repartition levels below a segment
 constexpr int SAMPLE2 = 4096;        // sample size of an in-bucket repartition
 
-// keys per thread of the shared-memory bucket sort: 16 for 4-byte keys, 8 for 8-byte keys
-template <class O> struct LeafIT { static constexpr int v = sizeof(O) == 4 ? 16 : 8; };
-template <class O> struct Cap { static constexpr int v = BK_NT * LeafIT<O>::v; };
+// Largest segment the shared-memory bucket sort takes: 8192 keys of 4 bytes,
+// 4096 of 8 bytes.
+template <class O> struct Cap { static constexpr int v = sizeof(O) == 4 ? 8192 : 4096; };
+// Threads and keys per thread of the leaf sort: keys alone use 256 threads with
+// 32 (4-byte) or 16 (8-byte) keys each; (key, position) pairs use 512 threads
+// with half as many, to stay within 64 registers.
+template <class O, bool HV> struct LeafCfg {
+    static constexpr int NT = HV ? 512 : 256;
+    static constexpr int IT = Cap<O>::v / NT;
+};
 
 // Error bits of the device status word.
 constexpr uint32_t ERR_DEPTH = 1u;         // a bucket still too large at MAX_DEPTH

@@ -84,12 +84,13 @@ void segment_sort(Ctx& c, SegSpec ss, const typename KT::T* src, const uint32_t*
         wl.part[1] = c.ar.take<WorkItem>(wl.part_cap);
     }
     if (!c.live()) return;
-    const size_t leaf_smem = HV ? LeafSmem<KT, HV>::bytes : PartLeafSmem<KT>::bytes;
+    const size_t leaf_smem = LeafSmem<KT, HV>::bytes;
     cudaFuncSetAttribute(k_leaf<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf_smem);
-    const uint32_t grid_l = (uint32_t)(c.num_sms * occupancy(k_leaf<KT, HV>, BK_NT, leaf_smem));
+    constexpr int LNT = LeafCfg<O, HV>::NT;
+    const uint32_t grid_l = (uint32_t)(c.num_sms * occupancy(k_leaf<KT, HV>, LNT, leaf_smem));
     if (direct) {
         OS_LAUNCH(c.st, c.nested ? "k_leaf.sample" : "k_leaf",
-                  k_leaf<KT, HV><<<std::min(ss.nseg, grid_l), BK_NT, leaf_smem, c.st>>>(true, ss, bufs, wl, seed, c.status));
+                  k_leaf<KT, HV><<<std::min(ss.nseg, grid_l), LNT, leaf_smem, c.st>>>(true, ss, bufs, wl, seed, c.status));
         return;
     }
     os_memset_async(wl.counts, 0, sizeof(uint32_t) * (MAX_DEPTH + 1), c.st);
@@ -101,12 +102,19 @@ void segment_sort(Ctx& c, SegSpec ss, const typename KT::T* src, const uint32_t*
                   k_repart<KT, HV><<<g, BK_NT, L::bytes, c.st>>>(level, ss, bufs, wl, seed, c.status, c.status + 1,
                                                                  reinterpret_cast<unsigned long long*>(c.status + 4)));
     }
-    OS_LAUNCH(c.st, c.nested ? "k_leaf.sample" : "k_leaf", k_leaf<KT, HV><<<grid_l, BK_NT, leaf_smem, c.st>>>(false, ss, bufs, wl, seed, c.status));
+    OS_LAUNCH(c.st, c.nested ? "k_leaf.sample" : "k_leaf", k_leaf<KT, HV><<<grid_l, LNT, leaf_smem, c.st>>>(false, ss, bufs, wl, seed, c.status));
+}
+
+// Bins of the top-level splitter table: the power of two >= 2p (at most 2^13).
+inline int table_lbits(uint32_t p) {
+    int b = 1;
+    while ((1u << b) < 2 * p && b < 13) ++b;
+    return b;
 }
 
 template <class KT>
-size_t classify_smem(int p, int P) {
-    return (size_t)Tree<typename KT::O>::node_bytes * P + sizeof(uint32_t) * p;
+size_t classify_smem(int p, int lbits) {
+    return split_table_bytes<typename KT::O>(p - 1, lbits) + sizeof(uint32_t) * (p + 1);
 }
 
 template <class KT, bool HV>
@@ -125,21 +133,20 @@ template <class KT, bool HV>
 void partition_top(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, uint32_t n,
                    const typename KT::O* spl_o, const uint32_t* spl_t, uint32_t p, typename KT::T* dst,
                    uint32_t* vdst, uint32_t* boff, uint32_t* bsize) {
-    const uint32_t P = pow2_ceil(p);
-    const int h = log2_exact(P);
+    const int lb = table_lbits(p);
     const uint32_t ntiles = (n + TOP_TILE - 1) / TOP_TILE;
     const uint32_t gmax = std::min<uint32_t>(std::max<uint32_t>(ntiles, 1), G_CAP);
     uint32_t* hist = c.ar.take<uint32_t>((size_t)p * gmax);
     uint32_t* col = c.ar.take<uint32_t>((size_t)p * gmax);
     uint16_t* bid = c.ar.take<uint16_t>(n);
     if (!c.live()) return;
-    const size_t sm_c = classify_smem<KT>(p, P), sm_s = scatter_smem<KT, HV>(p);
+    const size_t sm_c = classify_smem<KT>(p, lb), sm_s = scatter_smem<KT, HV>(p);
     cudaFuncSetAttribute(k_classify<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c);
     cudaFuncSetAttribute(k_scatter<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_s);
     const int occ = occupancy(k_scatter<KT, HV>, TOP_NT, sm_s);
     const uint32_t G = std::max<uint32_t>(1, std::min<uint32_t>(gmax, (uint32_t)(c.num_sms * occ)));
     OS_LAUNCH(c.st, c.nested ? "k_classify.sample" : "k_classify",
-              k_classify<KT><<<G, TOP_NT, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, h, hist, bid, ntiles));
+              k_classify<KT><<<G, TOP_NT, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, lb, hist, bid, ntiles));
     OS_LAUNCH(c.st, c.nested ? "k_column_scan.sample" : "k_column_scan",
               k_column_scan<<<grid_for((uint64_t)p * 32, 256), 256, 0, c.st>>>(hist, p, G, col, bsize));
     OS_LAUNCH(c.st, c.nested ? "k_bucket_offsets.sample" : "k_bucket_offsets", k_bucket_offsets<<<1, 1024, 0, c.st>>>(bsize, p, boff));

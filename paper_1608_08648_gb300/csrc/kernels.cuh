@@ -10,108 +10,13 @@
 //   step 5 (sort every bucket)          k_repart + k_leaf over the p buckets
 #pragma once
 
-#include "bitonic.cuh"
 #include "blocksort.cuh"
+#include "classify.cuh"
+#include "warp.cuh"
+#include "mergesort.cuh"
 #include "common.cuh"
 
 namespace ossort {
-
-// ---------------------------------------------------------------------------
-// Splitter search tree in shared memory: the p-1 tagged splitters (padded with
-// +inf up to P-1, P a power of two) in breadth-first (Eytzinger) order, so the
-// bucket of a key is found with log2(P) branch-free steps.
-// The bucket of x is the number of splitters strictly below x in the tagged
-// order (Section 2.2), so a key equal to a splitter closes the lower bucket.
-// ---------------------------------------------------------------------------
-template <class O> struct Tree;
-
-template <> struct Tree<uint32_t> {
-    uint64_t* c;
-    static constexpr int node_bytes = 8;
-    __device__ __forceinline__ void bind(char* p, int) { c = reinterpret_cast<uint64_t*>(p); }
-    __device__ __forceinline__ void set(int v, uint32_t o, uint32_t t) { c[v] = ((uint64_t)o << 32) | t; }
-    __device__ __forceinline__ void set_inf(int v) { c[v] = ~0ull; }
-    __device__ __forceinline__ int find(uint32_t o, uint32_t t, int h) const {
-        const uint64_t x = ((uint64_t)o << 32) | t;
-        int v = 1;
-        for (int d = 0; d < h; ++d) v = 2 * v + (x > c[v] ? 1 : 0);
-        return v - (1 << h);
-    }
-    // N searches advanced level by level, so their shared-memory loads overlap.
-    // Key i has tag t0 + i * dt.
-    template <int N>
-    __device__ __forceinline__ void find_n(const uint32_t (&o)[N], uint32_t t0, uint32_t dt, int h, int (&v)[N]) const {
-#pragma unroll
-        for (int i = 0; i < N; ++i) v[i] = 1;
-        for (int d = 0; d < h; ++d) {
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-                const uint64_t x = ((uint64_t)o[i] << 32) | (t0 + i * dt);
-                v[i] = 2 * v[i] + (x > c[v[i]] ? 1 : 0);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < N; ++i) v[i] -= 1 << h;
-    }
-};
-
-template <> struct Tree<uint64_t> {
-    uint64_t* o_;
-    uint32_t* t_;
-    static constexpr int node_bytes = 12;
-    __device__ __forceinline__ void bind(char* p, int P) {
-        o_ = reinterpret_cast<uint64_t*>(p);
-        t_ = reinterpret_cast<uint32_t*>(p + sizeof(uint64_t) * P);
-    }
-    __device__ __forceinline__ void set(int v, uint64_t o, uint32_t t) { o_[v] = o; t_[v] = t; }
-    __device__ __forceinline__ void set_inf(int v) { o_[v] = ~0ull; t_[v] = ~0u; }
-    __device__ __forceinline__ int find(uint64_t o, uint32_t t, int h) const {
-        int v = 1;
-        for (int d = 0; d < h; ++d) {
-            const uint64_t so = o_[v];
-            v = 2 * v + (((o > so) | ((o == so) & (t > t_[v]))) ? 1 : 0);
-        }
-        return v - (1 << h);
-    }
-    template <int N>
-    __device__ __forceinline__ void find_n(const uint64_t (&o)[N], uint32_t t0, uint32_t dt, int h, int (&v)[N]) const {
-#pragma unroll
-        for (int i = 0; i < N; ++i) v[i] = 1;
-        for (int d = 0; d < h; ++d) {
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-                const uint64_t so = o_[v[i]];
-                const uint32_t t = t0 + i * dt;
-                v[i] = 2 * v[i] + (((o[i] > so) | ((o[i] == so) & (t > t_[v[i]]))) ? 1 : 0);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < N; ++i) v[i] -= 1 << h;
-    }
-};
-
-// In-order rank (1-based) of Eytzinger node v in a complete tree of height h.
-__device__ __forceinline__ int eytz_rank(int v, int h) {
-    const int d = 31 - __clz(v);
-    return (2 * (v - (1 << d)) + 1) << (h - 1 - d);
-}
-
-// Fill the tree from sorted splitter arrays spl_o / spl_t of length p-1.
-template <class O>
-__device__ void tree_from_arrays(Tree<O>& tr, const O* spl_o, const uint32_t* spl_t, int p, int h) {
-    const int P = 1 << h;
-    for (int v = threadIdx.x + 1; v < P; v += blockDim.x) {
-        const int i = eytz_rank(v, h);
-        if (i < p) tr.set(v, spl_o[i - 1], spl_t[i - 1]);
-        else tr.set_inf(v);
-    }
-}
-
-__device__ __forceinline__ unsigned lanemask_lt() {
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
 
 // In-place exclusive scan of a[0, len) in shared memory by the whole block;
 // returns the total.  scratch: 32 words.  Starts and ends with __syncthreads.
@@ -224,41 +129,38 @@ __host__ __device__ inline uint32_t tile_lo(uint32_t g, uint32_t G, uint32_t nti
 template <class KT>
 __global__ void __launch_bounds__(TOP_NT, 3)
 k_classify(const typename KT::T* __restrict__ keys, uint32_t n, const typename KT::O* __restrict__ spl_o,
-           const uint32_t* __restrict__ spl_t, int p, int h, uint32_t* __restrict__ hist, uint16_t* __restrict__ bid,
-           uint32_t ntiles) {
+           const uint32_t* __restrict__ spl_t, int p, int lbits, uint32_t* __restrict__ hist,
+           uint16_t* __restrict__ bid, uint32_t ntiles) {
     using O = typename KT::O;
     extern __shared__ __align__(16) char smem[];
-    const int P = 1 << h;
-    Tree<O> tr;
-    tr.bind(smem, P);
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + Tree<O>::node_bytes * P);
-    tree_from_arrays<O>(tr, spl_o, spl_t, p, h);
-    for (int b = threadIdx.x; b < p; b += TOP_NT) cnt[b] = 0;
+    SplitTable<O> tb;
+    tb.bind(smem, p - 1, lbits);
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + split_table_bytes<O>(p - 1, lbits));   // [p + 1]
+    for (int i = threadIdx.x; i < p - 1; i += TOP_NT) tb.set(i, spl_o[i], spl_t[i]);
+    for (int b = threadIdx.x; b <= p; b += TOP_NT) cnt[b] = 0;
     __syncthreads();
+    split_table_finish<O>(tb, p - 1, lbits);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t G = gridDim.x, g = blockIdx.x;
     const uint32_t t0 = tile_lo(g, G, ntiles), t1 = tile_lo(g + 1, G, ntiles);
     for (uint32_t t = t0; t < t1; ++t) {
         const uint32_t base = t * TOP_TILE + w * (TOP_IT * 32) + lane;
         O o[TOP_IT];
-        int bk[TOP_IT];
 #pragma unroll
         for (int i = 0; i < TOP_IT; ++i) {
             const uint32_t e = base + i * 32;
             o[i] = e < n ? KT::ord(keys[e]) : O(0);
         }
-        tr.template find_n<TOP_IT>(o, base, 32, h, bk);
 #pragma unroll
         for (int i = 0; i < TOP_IT; ++i) {
             const uint32_t e = base + i * 32;
             const bool valid = e < n;
-            const unsigned act = __ballot_sync(0xffffffffu, valid);
+            int b = p;                       // past the end: a spare counter
             if (valid) {
-                const int b = bk[i];
+                b = split_find<O>(tb, o[i], e);
                 bid[e] = (uint16_t)b;
-                const unsigned m = __match_any_sync(act, b);
-                if (lane == __ffs(m) - 1) atomicAdd(&cnt[b], __popc(m));
             }
+            warp_count((uint32_t)b, cnt);
         }
     }
     __syncthreads();
@@ -306,10 +208,10 @@ static __global__ void k_bucket_offsets(const uint32_t* __restrict__ bsize, uint
 // (and payloads) into their buckets, using the bucket ids of pass 1.  Keys are
 // staged in shared memory grouped by bucket and written out as contiguous runs.
 // With a payload the scatter is stable: a key's rank among the tile's keys of
-// its bucket comes from per-warp counters (__match_any_sync groups) plus a
+// its bucket comes from per-warp counters (peer masks from ballots) plus a
 // cross-warp prefix, so every bucket receives its keys in input order.  Keys
-// alone need no order inside a bucket (equal keys are identical), so a
-// warp-aggregated shared-memory atomic hands out the slots.
+// alone need no order inside a bucket (equal keys are identical), so
+// shared-memory atomics, one per run of equal neighbours, hand out the slots.
 // ---------------------------------------------------------------------------
 template <class KT, bool HV>
 __global__ void __launch_bounds__(TOP_NT, 3)
@@ -353,10 +255,11 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
         }
         __syncthreads();   // counters cleared; previous tile fully written out
         if (HV) {
+            const int nbits = 32 - __clz(p);     // bucket ids 0..p fit
 #pragma unroll
             for (int i = 0; i < TOP_IT; ++i) {
                 const int b = (int)br[i];
-                const unsigned m = __match_any_sync(0xffffffffu, b);
+                const unsigned m = warp_peers((uint32_t)b, nbits);
                 const uint32_t c0 = mycnt[b];
                 br[i] = ((uint32_t)b << 16) | (c0 + __popc(m & lanemask_lt()));
                 __syncwarp();
@@ -378,13 +281,8 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
         } else {
 #pragma unroll
             for (int i = 0; i < TOP_IT; ++i) {
-                const int b = (int)br[i];
-                const unsigned m = __match_any_sync(0xffffffffu, b);
-                const int leader = __ffs(m) - 1;
-                uint32_t c0 = 0;
-                if (lane == leader) c0 = atomicAdd(&tile_off[b], (uint32_t)__popc(m));
-                c0 = __shfl_sync(0xffffffffu, c0, leader);
-                br[i] = ((uint32_t)b << 16) | (c0 + __popc(m & lanemask_lt()));
+                const uint32_t b = br[i];
+                br[i] = (b << 16) | warp_slot(b, tile_off);
             }
         }
         const uint32_t tvalid = block_exclusive_scan(tile_off, p, scratch);
@@ -457,25 +355,25 @@ __device__ __forceinline__ void seg_bounds(const SegSpec& ss, uint32_t k, uint32
 template <class KT, bool HV>
 struct BucketSmem {
     using O = typename KT::O;
-    static constexpr int IT = LeafIT<O>::v;
     static constexpr int CAP = Cap<O>::v;
     static constexpr size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
     static constexpr size_t sk_bytes = al16(sizeof(O) * padded_len<O>(CAP));
     static constexpr size_t sv_bytes = al16(sizeof(uint32_t) * padded_len<uint32_t>(CAP));
     static constexpr size_t sb_bytes = al16(sizeof(uint16_t) * CAP);
-    static constexpr size_t tree_bytes = al16(Tree<O>::node_bytes * MAXP2);
+    static constexpr size_t tree_bytes = al16(split_table_bytes<O>(MAXP2 - 1, MAXP2_LBITS));
     static constexpr size_t cnt_bytes = al16(sizeof(uint16_t) * BK_WARPS * (MAXP2 + 1));
     static constexpr size_t small_bytes = sizeof(uint32_t) * (4 * (MAXP2 + 1) + 32);
     static constexpr size_t bytes = sk_bytes + sv_bytes + sb_bytes + tree_bytes + cnt_bytes + small_bytes + 64;
 };
 
-// Shared memory of one leaf sort: the exchange area of the bitonic network
-// (which also stages the keys) and, with a payload, the payloads in input order.
+// Shared memory of one leaf sort: the exchange area of the merge sort (which
+// also stages the keys) and, with a payload, the payloads in input order.
 template <class KT, bool HV>
 struct LeafSmem {
     using O = typename KT::O;
     using E = typename LeafElem<O, HV>::E;
-    static constexpr int IT = LeafIT<O>::v;
+    static constexpr int NT = LeafCfg<O, HV>::NT;
+    static constexpr int IT = LeafCfg<O, HV>::IT;
     static constexpr int CAP = Cap<O>::v;
     static constexpr size_t ex_bytes = (sizeof(E) * padded_len<E>(CAP) + 15) & ~size_t(15);
     static constexpr size_t bytes = ex_bytes + (HV ? sizeof(uint32_t) * CAP : 0);
@@ -483,205 +381,34 @@ struct LeafSmem {
 
 // Sort [beg, beg+len) of `in` (len <= CAP) into the same range of `out`.
 template <class KT, bool HV>
-__device__ void leaf_sort(const typename KT::T* in, const uint32_t* vin, typename KT::T* out, uint32_t* vout,
+__device__ __forceinline__ void leaf_sort(const typename KT::T* in, const uint32_t* vin, typename KT::T* out, uint32_t* vout,
                           uint32_t beg, uint32_t len, char* smem) {
     using O = typename KT::O;
     using LE = LeafElem<O, HV>;
     using E = typename LE::E;
     using LS = LeafSmem<KT, HV>;
-    constexpr int IT = LS::IT;
+    constexpr int IT = LS::IT, NT = LS::NT;
     E* ex = reinterpret_cast<E*>(smem);
     uint32_t* sv = reinterpret_cast<uint32_t*>(smem + LS::ex_bytes);
-    int total = sort_extent<IT>((int)len);
-    if (total < 32 * IT) total = 32 * IT;
-    for (int j = threadIdx.x; j < total; j += BK_NT) {
-        ex[pad_idx<E>(j)] = LE::make(j < (int)len ? KT::ord(in[beg + j]) : OMax<O>::v, (uint32_t)j);
-        if (HV && j < (int)len) sv[j] = vin[beg + j];
+    for (int j = threadIdx.x; j < (int)len; j += NT) {
+        ex[pad_idx<E>(j)] = LE::make(KT::ord(in[beg + j]), (uint32_t)j);
+        if (HV) sv[j] = vin[beg + j];
     }
     __syncthreads();
     E x[IT];
     const int base = threadIdx.x * IT;
-    if (base < total) {
 #pragma unroll
-        for (int i = 0; i < IT; ++i) x[i] = ex[pad_idx<E>(base + i)];
-    }
-    bitonic_block<E, BK_NT, IT>(x, ex, total);
-    __syncthreads();
-    if (base < total) {
+    for (int i = 0; i < IT; ++i) x[i] = base + i < (int)len ? ex[pad_idx<E>(base + i)] : EMax<E>::v();
+    merge_sort_block<E, NT, IT>(x, ex, (int)len);
 #pragma unroll
-        for (int i = 0; i < IT; ++i) ex[pad_idx<E>(base + i)] = x[i];
-    }
+    for (int i = 0; i < IT; ++i)
+        if (base + i < (int)len) ex[pad_idx<E>(base + i)] = x[i];
     __syncthreads();
-    for (int j = threadIdx.x; j < (int)len; j += BK_NT) {
+    for (int j = threadIdx.x; j < (int)len; j += NT) {
         const E y = ex[pad_idx<E>(j)];
         out[beg + j] = KT::key(LE::key(y));
         if (HV) vout[beg + j] = sv[LE::pos(y)];
     }
-    __syncthreads();
-}
-
-// Keys-only leaf sort with one sample-sort level inside shared memory: a
-// stratified sample of the segment gives p3 - 1 tagged splitters (p3 <= 64), every
-// key is classified from registers and dropped into its sub-bucket of the
-// staging buffer (slots from warp-aggregated atomics: order inside a sub-bucket
-// is free for keys alone), the 32 16-lane groups then sort the sub-buckets (two
-// each) with the register bitonic network, and the finished segment is copied
-// out coalesced.  A segment whose largest sub-bucket exceeds a group's capacity
-// (rare) falls back to the block-wide bitonic sort.
-template <class O> struct PartLeaf {
-    static constexpr int LIT = LeafIT<O>::v;            // keys per thread while classifying
-    static constexpr int GIT = LeafIT<O>::v;            // keys per lane of a group sort
-    static constexpr int GCAP = 16 * GIT;               // keys one 16-lane group sorts
-    static constexpr int GROUPS = BK_NT / 16;
-    static constexpr int MAXP3 = 2 * GROUPS;            // sub-buckets (two per group)
-    static constexpr int SAMPLE3 = 1024;
-};
-
-template <class KT>
-struct PartLeafSmem {
-    using O = typename KT::O;
-    using PL = PartLeaf<O>;
-    static constexpr size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
-    static constexpr size_t b_bytes = al16(sizeof(O) * padded_len<O>(Cap<O>::v));
-    static constexpr size_t sv_bytes = al16(sizeof(uint32_t) * padded_len<uint32_t>(PL::SAMPLE3));
-    static constexpr size_t tree_bytes = al16(Tree<O>::node_bytes * PL::MAXP3);
-    static constexpr size_t small_bytes = sizeof(uint32_t) * (2 * (PL::MAXP3 + 1) + 32 + 4);
-    static constexpr size_t own = b_bytes + sv_bytes + tree_bytes + small_bytes;
-    static constexpr size_t bytes = own > LeafSmem<KT, false>::bytes ? own : LeafSmem<KT, false>::bytes;
-};
-
-template <class KT>
-__device__ void part_leaf_sort(const typename KT::T* in, typename KT::T* out, uint32_t beg, uint32_t len,
-                               char* smem, uint64_t seed) {
-    using O = typename KT::O;
-    using PL = PartLeaf<O>;
-    using PS = PartLeafSmem<KT>;
-    using LE = LeafElem<O, false>;
-    using E = typename LE::E;
-    constexpr int LIT = PL::LIT, GIT = PL::GIT, GCAP = PL::GCAP, MAXP3 = PL::MAXP3;
-    char* q = smem;
-    O* B = reinterpret_cast<O*>(q);                 q += PS::b_bytes;
-    uint32_t* sv = reinterpret_cast<uint32_t*>(q);  q += PS::sv_bytes;
-    Tree<O> tr;
-    tr.bind(q, MAXP3);                               q += PS::tree_bytes;
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(q); q += sizeof(uint32_t) * (MAXP3 + 1);
-    uint32_t* scratch = reinterpret_cast<uint32_t*>(q + sizeof(uint32_t) * (MAXP3 + 1));
-    uint32_t* flag = scratch + 32;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int grp = tid >> 4, gl = tid & 15;
-
-    if (len <= (uint32_t)GCAP) {
-        // One group sorts the whole segment straight from global memory.
-        if (w == 0) {
-            E x[GIT];
-            int ext = 1;
-            while (ext < (int)len) ext <<= 1;
-#pragma unroll
-            for (int i = 0; i < GIT; ++i) {
-                const int e = gl * GIT + i;
-                x[i] = E{(grp == 0 && e < (int)len) ? KT::ord(in[beg + e]) : OMax<O>::v};
-            }
-            bitonic_group16<E, GIT>(x, ext);
-            if (grp == 0) {
-#pragma unroll
-                for (int i = 0; i < GIT; ++i) {
-                    const int e = gl * GIT + i;
-                    if (e < (int)len) out[beg + e] = KT::key(LE::key(x[i]));
-                }
-            }
-        }
-        __syncthreads();
-        return;
-    }
-
-    // 1. Splitters from a stratified sample tagged with positions.
-    int p3 = 2;
-    while (p3 < MAXP3 && (uint32_t)p3 * (GCAP / 2) < len) p3 <<= 1;   // mean sub-bucket <= GCAP/2
-    const int h3 = 31 - __clz(p3);
-    int m3 = PL::SAMPLE3;
-    while ((uint32_t)m3 > len) m3 >>= 1;
-    const uint64_t state = sm_stream(seed ^ ((uint64_t)beg * SM_GAMMA), 11);
-    for (int j = tid; j < m3; j += BK_NT) {
-        const uint32_t lo = (uint32_t)((uint64_t)j * len / m3);
-        const uint32_t hi = (uint32_t)((uint64_t)(j + 1) * len / m3);
-        const uint32_t pos = lo + (uint32_t)(sm_at(state, j) % (uint64_t)max(hi - lo, 1u));
-        B[pad_idx<O>(j)] = KT::ord(in[beg + pos]);
-        sv[pad_idx<uint32_t>(j)] = pos;
-    }
-    block_merge_sort<O, true, BK_NT, 2>(B, sv, m3);
-    const int stride = m3 / p3;
-    for (int v = tid + 1; v < p3; v += BK_NT) {
-        const int i = eytz_rank(v, h3);
-        tr.set(v, B[pad_idx<O>(i * stride - 1)], sv[pad_idx<uint32_t>(i * stride - 1)]);
-    }
-    for (int b = tid; b <= p3; b += BK_NT) cnt[b] = 0;
-    if (tid == 0) *flag = 0;
-    __syncthreads();
-
-    // 2. Classify from registers; warp-aggregated atomic slots.
-    const uint32_t base = w * (LIT * 32) + lane;
-    O o[LIT];
-    uint32_t bs[LIT];   // sub-bucket << 16 | slot
-    {
-        int bk[LIT];
-#pragma unroll
-        for (int i = 0; i < LIT; ++i) {
-            const uint32_t e = base + i * 32;
-            o[i] = e < len ? KT::ord(in[beg + e]) : O(0);
-        }
-        tr.template find_n<LIT>(o, base, 32, h3, bk);
-#pragma unroll
-        for (int i = 0; i < LIT; ++i) {
-            const uint32_t e = base + i * 32;
-            const int b = e < len ? bk[i] : p3;
-            const unsigned m = __match_any_sync(0xffffffffu, b);
-            const int leader = __ffs(m) - 1;
-            uint32_t c0 = 0;
-            if (lane == leader) c0 = atomicAdd(&cnt[b], (uint32_t)__popc(m));
-            c0 = __shfl_sync(0xffffffffu, c0, leader);
-            bs[i] = ((uint32_t)b << 16) | (c0 + __popc(m & lanemask_lt()));
-        }
-    }
-    const uint32_t total = block_exclusive_scan(cnt, p3, scratch);
-    if (tid == 0) cnt[p3] = total;
-    __syncthreads();
-    if (tid < p3 && cnt[tid + 1] - cnt[tid] > (uint32_t)GCAP) atomicOr(flag, 1u);
-    // 3. Drop every key into its sub-bucket.
-#pragma unroll
-    for (int i = 0; i < LIT; ++i) {
-        const int b = (int)(bs[i] >> 16);
-        if (b < p3) B[pad_idx<O>(cnt[b] + (bs[i] & 0xFFFFu))] = o[i];
-    }
-    __syncthreads();
-    if (*flag) {
-        leaf_sort<KT, false>(in, nullptr, out, nullptr, beg, len, smem);
-        return;
-    }
-    // 4. Every 16-lane group sorts its sub-buckets in registers, in place.
-#pragma unroll 1
-    for (int sb = grp; sb < PL::GROUPS * 2; sb += PL::GROUPS) {
-        const uint32_t gb = sb < p3 ? cnt[sb] : 0u;
-        const int gm = sb < p3 ? (int)(cnt[sb + 1] - gb) : 0;
-        int ext = 1;
-        while (ext < gm) ext <<= 1;
-        ext = (int)__reduce_max_sync(0xffffffffu, (unsigned)ext);
-        if (ext <= 1 && gm == 0) continue;   // warp-uniform: both groups of the warp are empty
-        E x[GIT];
-#pragma unroll
-        for (int i = 0; i < GIT; ++i) {
-            const int e = gl * GIT + i;
-            x[i] = E{e < gm ? B[pad_idx<O>(gb + e)] : OMax<O>::v};
-        }
-        bitonic_group16<E, GIT>(x, ext);
-#pragma unroll
-        for (int i = 0; i < GIT; ++i) {
-            const int e = gl * GIT + i;
-            if (e < gm) B[pad_idx<O>(gb + e)] = LE::key(x[i]);
-        }
-    }
-    __syncthreads();
-    // 5. The sub-buckets are in order: copy the segment out coalesced.
-    for (uint32_t j = tid; j < len; j += BK_NT) out[beg + j] = KT::key(B[pad_idx<O>(j)]);
     __syncthreads();
 }
 
@@ -701,8 +428,8 @@ __device__ int cta_partition(const typename KT::T* in, const uint32_t* vin, type
     O* sk = reinterpret_cast<O*>(q);               q += L::sk_bytes;
     uint32_t* sv = reinterpret_cast<uint32_t*>(q); q += L::sv_bytes;
     uint16_t* sb = reinterpret_cast<uint16_t*>(q); q += L::sb_bytes;
-    Tree<O> tr;
-    tr.bind(q, MAXP2);                              q += L::tree_bytes;
+    SplitTable<O> stab;
+    stab.bind(q, MAXP2 - 1, MAXP2_LBITS);             q += L::tree_bytes;
     uint16_t* cnt = reinterpret_cast<uint16_t*>(q); q += L::cnt_bytes;
     uint32_t* part = reinterpret_cast<uint32_t*>(q);     q += sizeof(uint32_t) * (MAXP2 + 1);
     uint32_t* tile_off = reinterpret_cast<uint32_t*>(q); q += sizeof(uint32_t) * (MAXP2 + 1);
@@ -712,7 +439,7 @@ __device__ int cta_partition(const typename KT::T* in, const uint32_t* vin, type
     // Fan-out: children of about 5/8 CAP on average, at most MAXP2.
     int p2 = 2;
     while (p2 < MAXP2 && (uint64_t)p2 * (CAP * 5 / 8) < len) p2 <<= 1;
-    int h = 31 - __clz(p2);
+    const int lbits2 = 32 - __clz(p2);              // 2 p2 bins
     const int s2 = SAMPLE2 / p2;
     const int m2 = p2 * s2;
 
@@ -733,35 +460,27 @@ __device__ int cta_partition(const typename KT::T* in, const uint32_t* vin, type
     }
     static_assert(SAMPLE2 == BK_NT * IT, "the sample is sorted as one block of BK_NT x IT keys");
     block_merge_sort<O, true, BK_NT, IT>(sk, sv, m2);
-    for (int v = threadIdx.x + 1; v < p2; v += BK_NT) {
-        const int i = eytz_rank(v, h);
-        tr.set(v, sk[pad_idx<O>(i * s2 - 1)], sv[pad_idx<uint32_t>(i * s2 - 1)]);
-    }
+    for (int i = threadIdx.x + 1; i < p2; i += BK_NT)
+        stab.set(i - 1, sk[pad_idx<O>(i * s2 - 1)], sv[pad_idx<uint32_t>(i * s2 - 1)]);
     for (int b = threadIdx.x; b <= p2; b += BK_NT) part[b] = 0;
     __syncthreads();
+    split_table_finish<O>(stab, p2 - 1, lbits2);
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     // 2. Counting pass.
     for (uint32_t tb = 0; tb < len; tb += TILE) {
         const uint32_t base = tb + w * (IT * 32) + lane;
         O o[IT];
-        int bk[IT];
 #pragma unroll
         for (int i = 0; i < IT; ++i) {
             const uint32_t e = base + i * 32;
             o[i] = e < len ? KT::ord(in[beg + e]) : O(0);
         }
-        tr.template find_n<IT>(o, base, 32, h, bk);
 #pragma unroll
         for (int i = 0; i < IT; ++i) {
             const uint32_t e = base + i * 32;
-            const bool valid = e < len;
-            const unsigned act = __ballot_sync(0xffffffffu, valid);
-            if (valid) {
-                const int b = bk[i];
-                const unsigned m = __match_any_sync(act, b);
-                if (lane == __ffs(m) - 1) atomicAdd(&part[b], __popc(m));
-            }
+            const int b = e < len ? split_find<O>(stab, o[i], e) : p2;
+            warp_count((uint32_t)b, part);
         }
     }
     const uint32_t total = block_exclusive_scan(part, p2, scratch);
@@ -790,19 +509,16 @@ __device__ int cta_partition(const typename KT::T* in, const uint32_t* vin, type
             for (int b = threadIdx.x; b <= p2; b += BK_NT) tile_off[b] = 0;
         }
         __syncthreads();
-        {
-            O o[IT];
 #pragma unroll
-            for (int i = 0; i < IT; ++i) o[i] = KT::ord(kv[i]);
-            tr.template find_n<IT>(o, base, 32, h, bk);
-        }
+        for (int i = 0; i < IT; ++i) bk[i] = split_find<O>(stab, KT::ord(kv[i]), base + i * 32);
         if (HV) {
+            const int nbits = 32 - __clz(p2);
 #pragma unroll
             for (int i = 0; i < IT; ++i) {
                 const uint32_t e = base + i * 32;
                 const bool valid = e < len;
                 const int b = valid ? bk[i] : p2;
-                const unsigned m = __match_any_sync(0xffffffffu, b);
+                const unsigned m = warp_peers((uint32_t)b, nbits);
                 const uint32_t c0 = mycnt[b];
                 br[i] = ((uint32_t)b << 16) | (c0 + __popc(m & lanemask_lt()));
                 __syncwarp();
@@ -824,13 +540,8 @@ __device__ int cta_partition(const typename KT::T* in, const uint32_t* vin, type
 #pragma unroll
             for (int i = 0; i < IT; ++i) {
                 const uint32_t e = base + i * 32;
-                const int b = e < len ? bk[i] : p2;
-                const unsigned m = __match_any_sync(0xffffffffu, b);
-                const int leader = __ffs(m) - 1;
-                uint32_t c0 = 0;
-                if (lane == leader) c0 = atomicAdd(&tile_off[b], (uint32_t)__popc(m));
-                c0 = __shfl_sync(0xffffffffu, c0, leader);
-                br[i] = ((uint32_t)b << 16) | (c0 + __popc(m & lanemask_lt()));
+                const uint32_t b = e < len ? (uint32_t)bk[i] : (uint32_t)p2;
+                br[i] = (b << 16) | warp_slot(b, tile_off);
             }
         }
         const uint32_t tvalid = block_exclusive_scan(tile_off, p2, scratch);
@@ -952,12 +663,11 @@ k_repart(int level, SegSpec ss, SortBufs<KT> bufs, WorkLists wl, uint64_t seed, 
 
 // Shared-memory sort of every leaf: the segments of ss directly (direct = true)
 // or the leaf list.  Persistent: CTAs stride over the work.
-// Resident leaf CTAs per SM the register budget is sized for: two, except for
-// 64-bit keys with a payload, whose (key, position) elements need more registers.
-template <class KT, bool HV> struct LeafOcc { static constexpr int v = (sizeof(typename KT::O) == 8 && HV) ? 1 : 2; };
+// Resident leaf CTAs per SM the register budget is sized for (64 registers).
+template <class KT, bool HV> struct LeafOcc { static constexpr int v = 65536 / (64 * LeafCfg<typename KT::O, HV>::NT); };
 
 template <class KT, bool HV>
-__global__ void __launch_bounds__(BK_NT, LeafOcc<KT, HV>::v)
+__global__ void __launch_bounds__(LeafCfg<typename KT::O, HV>::NT, LeafOcc<KT, HV>::v)
 k_leaf(bool direct, SegSpec ss, SortBufs<KT> bufs, WorkLists wl, uint64_t seed, uint32_t* status) {
     using L = BucketSmem<KT, HV>;
     extern __shared__ __align__(16) char smem[];
@@ -978,8 +688,7 @@ k_leaf(bool direct, SegSpec ss, SortBufs<KT> bufs, WorkLists wl, uint64_t seed, 
             if (threadIdx.x == 0) flag_bounds(status, 6, (uint64_t)beg + len);
             continue;
         }
-        if (HV) leaf_sort<KT, HV>(bufs.key_buf(buf), bufs.val_buf(buf), bufs.out, bufs.vout, beg, len, smem);
-        else part_leaf_sort<KT>(bufs.key_buf(buf), bufs.out, beg, len, smem, seed);
+        leaf_sort<KT, HV>(bufs.key_buf(buf), bufs.val_buf(buf), bufs.out, bufs.vout, beg, len, smem);
     }
 }
 

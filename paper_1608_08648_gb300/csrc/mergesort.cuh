@@ -1,0 +1,109 @@
+// Block-wide merge sort of up to NT*IT elements held in registers (the
+// shared-memory bucket sort of step 5).
+//
+//  1. Every thread sorts its IT consecutive elements in registers with a
+//     bitonic network (compile-time compare-exchanges).
+//  2. log2(len / IT) rounds merge pairs of sorted runs through shared memory.
+//     In a round a thread owns IT consecutive outputs of its pair: a merge-path
+//     binary search finds how many of them come from the left run (ai) and the
+//     right run (bi).  Its outputs are then the IT smallest of A[ai, ai+IT) and
+//     B[bi, bi+IT); taking min(A[ai+i], B[bi+IT-1-i]) element by element yields
+//     exactly those IT elements as a bitonic sequence (the half-cleaner of a
+//     bitonic merge), which log2(IT) register stages sort.  Every step is data
+//     independent, so a thread's loads and compare-exchanges overlap.
+//
+// Runs need not be powers of two: positions at or beyond len read as +infinity,
+// so a ragged last run costs nothing extra.  The elements are compared whole
+// (E::lt); equal elements are interchangeable (keys alone, or unique
+// (key, position) pairs), so no stability rule is needed in the merge itself.
+#pragma once
+
+#include "blocksort.cuh"
+#include "common.cuh"
+#include "elements.cuh"
+
+namespace ossort {
+
+template <class E>
+__device__ __forceinline__ void cas_up(E& a, E& b) {   // a <- min, b <- max
+    const bool sw = E::lt(b, a);
+    const E lo = sw ? b : a, hi = sw ? a : b;
+    a = lo;
+    b = hi;
+}
+
+template <class E>
+__device__ __forceinline__ E emin(const E& a, const E& b) { return E::lt(b, a) ? b : a; }
+
+// Bitonic sort of x[0..IT) ascending (IT a power of two); every compare-exchange
+// and its direction are fixed at compile time.
+template <class E, int IT>
+__device__ __forceinline__ void bitonic_sort_regs(E (&x)[IT]) {
+#pragma unroll
+    for (int kk = 2; kk <= IT; kk <<= 1)
+#pragma unroll
+        for (int jj = kk >> 1; jj >= 1; jj >>= 1)
+#pragma unroll
+            for (int i = 0; i < IT; ++i)
+                if ((i & jj) == 0) {
+                    if ((i & kk) == 0) cas_up(x[i], x[i + jj]);
+                    else cas_up(x[i + jj], x[i]);
+                }
+}
+
+// Sort a bitonic sequence x[0..IT) ascending.
+template <class E, int IT>
+__device__ __forceinline__ void bitonic_merge_regs(E (&x)[IT]) {
+#pragma unroll
+    for (int jj = IT / 2; jj >= 1; jj >>= 1)
+#pragma unroll
+        for (int i = 0; i < IT; ++i)
+            if ((i & jj) == 0) cas_up(x[i], x[i + jj]);
+}
+
+// x: the thread's IT elements at positions tid*IT + i (blocked; positions >= len
+// must hold EMax).  sk: shared memory for padded_len<E>(NT*IT) elements.  On
+// return x holds the thread's IT outputs of the sorted sequence.  All NT threads
+// must call; starts and ends with __syncthreads.
+template <class E, int NT, int IT>
+__device__ __forceinline__ void merge_sort_block(E (&x)[IT], E* sk, int len) {
+    const int base = threadIdx.x * IT;
+    const bool active = base < len;
+    if (active) bitonic_sort_regs<E, IT>(x);
+    for (int run = IT; run < len; run *= 2) {
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int i = 0; i < IT; ++i)
+                if (base + i < len) sk[pad_idx<E>(base + i)] = x[i];
+        }
+        __syncthreads();
+        if (active) {
+            const int pb = base & ~(2 * run - 1);      // first position of the pair
+            const int d = base - pb;                   // output diagonal inside the pair
+            const int la = min(run, len - pb);
+            const int lb = max(0, min(run, len - pb - run));
+            const E* A = sk;                           // A[j] = sk[pb + j]
+            int lo = max(0, d - lb), hi = min(d, la);
+            while (lo < hi) {                          // left-run outputs among the first d
+                const int mid = (lo + hi) >> 1;
+                const E av = A[pad_idx<E>(pb + mid)];
+                const E bv = A[pad_idx<E>(pb + run + d - 1 - mid)];
+                if (E::lt(bv, av)) hi = mid;
+                else lo = mid + 1;
+            }
+            const int ai = lo, bi = d - lo;
+#pragma unroll
+            for (int i = 0; i < IT; ++i) {
+                const int ia = ai + i, ib = bi + IT - 1 - i;
+                const E av = ia < la ? A[pad_idx<E>(pb + ia)] : EMax<E>::v();
+                const E bv = ib < lb ? A[pad_idx<E>(pb + run + ib)] : EMax<E>::v();
+                x[i] = emin(av, bv);
+            }
+            bitonic_merge_regs<E, IT>(x);
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace ossort
