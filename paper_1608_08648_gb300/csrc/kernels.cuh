@@ -436,10 +436,11 @@ __device__ int cta_partition(const typename KT::T* in, const uint32_t* vin, type
     uint32_t* cursor = reinterpret_cast<uint32_t*>(q);   q += sizeof(uint32_t) * (MAXP2 + 1);
     uint32_t* scratch = reinterpret_cast<uint32_t*>(q);
 
-    // Fan-out: children of about 5/8 CAP on average, at most MAXP2.
-    int p2 = 2;
-    while (p2 < MAXP2 && (uint64_t)p2 * (CAP * 5 / 8) < len) p2 <<= 1;
-    const int lbits2 = 32 - __clz(p2);              // 2 p2 bins
+    // Fan-out: children of about 0.72 CAP on average (so that nearly all of a
+    // leaf sort's threads have keys and few children overflow), at most MAXP2.
+    const uint64_t want = ((uint64_t)len * 25 + 18 * (uint64_t)CAP - 1) / (18 * (uint64_t)CAP);
+    const int p2 = want < 2 ? 2 : (want > (uint64_t)MAXP2 ? MAXP2 : (int)want);
+    const int lbits2 = 32 - __clz(2 * p2 - 1);      // bins: the power of two >= 2 p2
     const int s2 = SAMPLE2 / p2;
     const int m2 = p2 * s2;
 
@@ -458,8 +459,12 @@ __device__ int cta_partition(const typename KT::T* in, const uint32_t* vin, type
         sk[pad_idx<O>(j)] = KT::ord(in[beg + pos]);
         sv[pad_idx<uint32_t>(j)] = pos;
     }
+    for (int j = m2 + threadIdx.x; j < SAMPLE2; j += BK_NT) {   // pad to a full block: sorts last
+        sk[pad_idx<O>(j)] = OMax<O>::v;
+        sv[pad_idx<uint32_t>(j)] = 0xFFFFFFFFu;
+    }
     static_assert(SAMPLE2 == BK_NT * IT, "the sample is sorted as one block of BK_NT x IT keys");
-    block_merge_sort<O, true, BK_NT, IT>(sk, sv, m2);
+    block_merge_sort<O, true, BK_NT, IT>(sk, sv, SAMPLE2);
     for (int i = threadIdx.x + 1; i < p2; i += BK_NT)
         stab.set(i - 1, sk[pad_idx<O>(i * s2 - 1)], sv[pad_idx<uint32_t>(i * s2 - 1)]);
     for (int b = threadIdx.x; b <= p2; b += BK_NT) part[b] = 0;

@@ -12,8 +12,9 @@
 //     bitonic merge), which log2(IT) register stages sort.  Every step is data
 //     independent, so a thread's loads and compare-exchanges overlap.
 //
-// Runs need not be powers of two: positions at or beyond len read as +infinity,
-// so a ragged last run costs nothing extra.  The elements are compared whole
+// Runs are padded: every thread stores all IT of its elements, and positions at
+// or beyond len hold +infinity, so a ragged last run needs no special case.  The
+// shared buffer therefore spans NT*IT positions.  The elements are compared whole
 // (E::lt); equal elements are interchangeable (keys alone, or unique
 // (key, position) pairs), so no stability rule is needed in the merge itself.
 #pragma once
@@ -62,7 +63,8 @@ __device__ __forceinline__ void bitonic_merge_regs(E (&x)[IT]) {
 }
 
 // x: the thread's IT elements at positions tid*IT + i (blocked; positions >= len
-// must hold EMax).  sk: shared memory for padded_len<E>(NT*IT) elements.  On
+// must hold EMax).  sk: shared memory for padded_len<E>(NT*IT) elements; the
+// whole block must hold NT*IT >= len.  On
 // return x holds the thread's IT outputs of the sorted sequence.  All NT threads
 // must call; starts and ends with __syncthreads.
 template <class E, int NT, int IT>
@@ -71,20 +73,20 @@ __device__ __forceinline__ void merge_sort_block(E (&x)[IT], E* sk, int len) {
     const bool active = base < len;
     if (active) bitonic_sort_regs<E, IT>(x);
     for (int run = IT; run < len; run *= 2) {
-        __syncthreads();
-        if (active) {
+        // A pair of runs that fits in one warp's elements is merged by that warp
+        // alone, so only the larger rounds need the whole block.
+        const bool block_wide = 2 * run > 32 * IT;
+        if (block_wide) __syncthreads();
+        else __syncwarp();
 #pragma unroll
-            for (int i = 0; i < IT; ++i)
-                if (base + i < len) sk[pad_idx<E>(base + i)] = x[i];
-        }
-        __syncthreads();
+        for (int i = 0; i < IT; ++i) sk[pad_idx<E>(base + i)] = x[i];   // beyond len: +infinity
+        if (block_wide) __syncthreads();
+        else __syncwarp();
         if (active) {
             const int pb = base & ~(2 * run - 1);      // first position of the pair
             const int d = base - pb;                   // output diagonal inside the pair
-            const int la = min(run, len - pb);
-            const int lb = max(0, min(run, len - pb - run));
             const E* A = sk;                           // A[j] = sk[pb + j]
-            int lo = max(0, d - lb), hi = min(d, la);
+            int lo = max(0, d - run), hi = min(d, run);
             while (lo < hi) {                          // left-run outputs among the first d
                 const int mid = (lo + hi) >> 1;
                 const E av = A[pad_idx<E>(pb + mid)];
@@ -96,8 +98,8 @@ __device__ __forceinline__ void merge_sort_block(E (&x)[IT], E* sk, int len) {
 #pragma unroll
             for (int i = 0; i < IT; ++i) {
                 const int ia = ai + i, ib = bi + IT - 1 - i;
-                const E av = ia < la ? A[pad_idx<E>(pb + ia)] : EMax<E>::v();
-                const E bv = ib < lb ? A[pad_idx<E>(pb + run + ib)] : EMax<E>::v();
+                const E av = ia < run ? A[pad_idx<E>(pb + ia)] : EMax<E>::v();
+                const E bv = ib < run ? A[pad_idx<E>(pb + run + ib)] : EMax<E>::v();
                 x[i] = emin(av, bv);
             }
             bitonic_merge_regs<E, IT>(x);
