@@ -39,11 +39,11 @@ def parse():
     ap.add_argument("--dtype", default="i32", choices=["i32", "f64", "u64"])
     ap.add_argument("--dist", default="uniform")
     ap.add_argument("--split", default="ran", choices=["ran", "det"])
-    ap.add_argument("--n", type=int, default=1 << 28)
+    ap.add_argument("--keys", type=int, default=1 << 28, help="n, the number of keys")
     ap.add_argument("--p", type=int, default=1024)
     ap.add_argument("--s", type=int, default=16)
     ap.add_argument("--seed", type=int, default=1)
-    ap.add_argument("--cpu-sample", type=int, default=1 << 22, help="keys of the oracle's timed sample")
+    ap.add_argument("--cpu-sample", type=int, default=1 << 25, help="keys of the oracle's timed sample")
     ap.add_argument("--ref-sample", type=int, default=1 << 20, help="keys per step of --impl reference")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -140,7 +140,36 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
-# ---- algorithmic bytes ------------------------------------------------------------
+# ---- algorithmic bytes and measured traffic ---------------------------------------
+
+def cuda_source_sha() -> str:
+    """sha256 prefix over the CUDA sources and the ABI header (same recipe as profiles/)."""
+    import glob
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1608_08648_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")))
+    files.append(os.path.join(ROOT, "include", "ossort.h"))
+    h = hashlib.sha256()
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, dtype: str, n: int):
+    """DRAM bytes of one step of `kernel` from the committed ncu capture, scaled by n;
+    None when the kernels changed since the capture or no capture exists."""
+    path = os.path.join(ROOT, "profiles", f"kernel_traffic_{dtype}.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except OSError:
+        return None
+    if t.get("source_sha") != cuda_source_sha() or kernel not in t.get("dram_bytes_per_key", {}):
+        return None
+    return int(t["dram_bytes_per_key"][kernel] * n)
+
 
 def algorithmic_bytes(name: str, n: int, kb: int, vb: int, repart_keys: int) -> int:
     """Bytes a kernel must move for one step (one full sort of n keys):
@@ -169,7 +198,7 @@ def run_ours(a, rank, world, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    n = a.n
+    n = a.keys
     kt = oss.KEY_TYPES[a.dtype]
     kb, vb = KEY_BYTES[a.dtype], 0
     keys = inputs.keys(a.dist, n, a.dtype, seed=a.seed + rank, p=a.p, device=dev)
@@ -253,6 +282,19 @@ def run_ours(a, rank, world, local):
         e2e = {"value": world * n / t, "unit": "keys/s", "ms_per_step": t * 1e3,
                "h2d_bytes_per_step": n * kb, "d2h_bytes_per_step": n * kb}
 
+    # context: torch.sort (CUB radix sort, values and int64 indices) of the same keys
+    tk = keys.view(torch.int64) if a.dtype == "u64" else keys
+    for _ in range(2):
+        torch.sort(tk)
+    t0e = torch.cuda.Event(enable_timing=True)
+    t1e = torch.cuda.Event(enable_timing=True)
+    t0e.record(stream)
+    for _ in range(3):
+        torch.sort(tk)
+    t1e.record(stream)
+    torch.cuda.synchronize()
+    torch_sort_ms = t0e.elapsed_time(t1e) / 3
+
     # roofline of the dominant kernel (top-level launches only)
     peaks, peak_kind = measured_peaks()
     top = [k for k in prof if not k["name"].endswith(".sample")]
@@ -263,7 +305,8 @@ def run_ours(a, rank, world, local):
         achieved = alg / (dom["total_ms"] / 1e3) / 1e9 if dom["total_ms"] > 0 else 0.0
         peak = float(peaks["hbm_gbs"])
         roof = {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": measured_traffic(dom["name"], a.dtype, n),
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "avg_launch_ms": round(dom["total_ms"] / dom["launches"], 4),
                 "alg_bytes_per_step": algorithmic_bytes(dom["name"], n, kb, vb, st["repart_keys"])}
@@ -279,7 +322,9 @@ def run_ours(a, rank, world, local):
            "kernels": [{"name": k["name"], "launches": k["launches"], "total_ms": round(k["total_ms"], 4),
                         "share": round(k["total_ms"] / max(1e-9, sum(x["total_ms"] for x in prof)), 4)}
                        for k in sorted(prof, key=lambda k: -k["total_ms"])],
-           "stats": {"max_bucket": st["max_bucket"], "depth": st["depth"], "repart_keys": st["repart_keys"]}}
+           "stats": {"max_bucket": st["max_bucket"], "depth": st["depth"], "repart_keys": st["repart_keys"]},
+           "context": {"torch_sort_ms": round(torch_sort_ms, 3),
+                       "note": "torch.sort of the same keys (radix sort returning values and indices), not a baseline"}}
     if rank == 0 and world == 1 and not a.no_cpu:
         res["cpu_baseline"] = cpu_baseline(a)
     return res
@@ -299,8 +344,8 @@ def cpu_baseline(a):
 
     import oracle
     from paper_1608_08648_gb300 import inputs
-    m = min(a.cpu_sample, a.n)
-    keys = inputs.keys(a.dist, a.n, a.dtype, seed=a.seed, p=a.p, count=m).numpy()
+    m = min(a.cpu_sample, a.keys)
+    keys = inputs.keys(a.dist, a.keys, a.dtype, seed=a.seed, p=a.p, count=m).numpy()
     if a.dtype == "u64":
         keys = keys.view(np.uint64)
     t0 = time.perf_counter()
@@ -319,8 +364,8 @@ def run_reference(a, rank, world):
     from paper_1608_08648_gb300 import inputs
     if rank != 0:
         return None
-    m = min(a.ref_sample, a.n)
-    keys = inputs.keys(a.dist, a.n, a.dtype, seed=a.seed, p=a.p, count=m).numpy()
+    m = min(a.ref_sample, a.keys)
+    keys = inputs.keys(a.dist, a.keys, a.dtype, seed=a.seed, p=a.p, count=m).numpy()
     if a.dtype == "u64":
         keys = keys.view(np.uint64)
     for _ in range(a.warmup):
@@ -333,7 +378,7 @@ def run_reference(a, rank, world):
     return {"impl": "reference", "metric": "keys/s", "value": v, "unit": "keys/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": a.dtype, "data": "synthetic",
-            "config": {"workload": workload_name(a, a.n), "n": a.n, "key": a.dtype, "dist": a.dist,
+            "config": {"workload": workload_name(a, a.keys), "n": a.keys, "key": a.dtype, "dist": a.dist,
                        "split": a.split, "p": a.p, "s": a.s, "seed": a.seed, "parallelism": "replicas"},
             "cpu_baseline": {"value": v, "unit": "keys/s", "kind": "oracle", "cores": 1,
                              "sample": f"first {m} keys of the workload per step"},
