@@ -157,6 +157,33 @@ int os_sort_host(int key_type, const void* h_keys_in, void* h_keys_out,
                  const os_params* prm, void* d_ws, size_t ws_bytes, void* stream);
 
 /*
+ * Sort without any device allocation by the caller.  (An addition of this
+ * library with no counterpart in the paper.)  For callers that may not
+ * allocate device memory -- code inside a framework that owns all device
+ * memory, or a path that must not allocate after start-up -- and so cannot
+ * provide the workspace os_sort asks for.  Same arguments and semantics as
+ * os_sort without d_ws, ws_bytes and stats; the workspace is a scratch array of
+ * OS_NOALLOC_SCRATCH_BYTES compiled into the library, held on every device
+ * where this entry point has been called until the process exits.
+ *  - A sort whose os_workspace_size exceeds OS_NOALLOC_SCRATCH_BYTES is refused
+ *    with OS_ERR_UNSUPPORTED before any work is enqueued (64 MiB holds, e.g.,
+ *    about 8.2 million int32 keys for SqRan p = 1024, s = 16 without payload).
+ *  - The first call on a device, with that device current, looks up the
+ *    scratch's device address (cudaGetSymbolAddress); make that first call
+ *    before any stream capture on the device.
+ *  - All calls on a device share the scratch: calls that overlap on the GPU
+ *    (on different streams without ordering) race and must be avoided.
+ *    Whatever must start at zero is cleared by every call.
+ *  - Device-side error flags stay in the scratch and are not reported here.
+ * Calls no allocating routine.
+ */
+#define OS_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+int os_sort_noalloc(int key_type, const void* d_keys_in, void* d_keys_out,
+                    const uint32_t* d_vals_in, uint32_t* d_vals_out, uint64_t n,
+                    const os_params* prm, void* stream);
+
+/*
  * Synchronize `stream` and read the device status word in the workspace of the
  * last sort enqueued with it: OS_OK, or OS_ERR_DEVICE with the raw error bits in
  * *bits (may be NULL).

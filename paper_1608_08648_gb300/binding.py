@@ -18,6 +18,7 @@ OS_STABLE = 1
 OS_MAX_N = 1 << 31
 OS_MAX_P = 4096
 OS_MAX_PS = 1 << 24
+OS_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 _u32, _u64, _i32, _vp, _sz = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t
 
@@ -69,6 +70,8 @@ def lib() -> ctypes.CDLL:
         L.os_sort_host.restype = ctypes.c_int
         L.os_sort_host.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp, _u64, ctypes.POINTER(os_params), _vp, _sz,
                                    _vp]
+        L.os_sort_noalloc.restype = ctypes.c_int
+        L.os_sort_noalloc.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp, _u64, ctypes.POINTER(os_params), _vp]
         L.os_launch_count.restype = _u64
         L.os_launch_count.argtypes = []
         L.os_profile_start.restype = ctypes.c_int
@@ -116,6 +119,12 @@ def os_sort_host(key_type: int, h_keys_in: int, h_keys_out: int, h_vals_in: int 
                  n: int, prm: os_params, d_ws: int, ws_bytes: int, stream: int | None) -> int:
     return lib().os_sort_host(key_type, h_keys_in, h_keys_out, h_vals_in, h_vals_out, n, ctypes.byref(prm), d_ws,
                               ws_bytes, stream)
+
+
+def os_sort_noalloc(key_type: int, d_keys_in: int, d_keys_out: int, d_vals_in: int | None,
+                    d_vals_out: int | None, n: int, prm: os_params, stream: int | None) -> int:
+    return lib().os_sort_noalloc(key_type, d_keys_in, d_keys_out, d_vals_in, d_vals_out, n, ctypes.byref(prm),
+                                 stream)
 
 
 def os_check(d_ws: int, stream: int | None) -> tuple[int, int]:
