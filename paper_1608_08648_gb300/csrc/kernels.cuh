@@ -323,8 +323,8 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
 // Step 5 (and step 1 of SqDet): sort every segment of an array.
 // A segment of at most CAP keys is sorted in shared memory by one CTA
 // (k_leaf, block_merge_sort).  A larger one is repartitioned by one CTA
-// (k_repart) -- the recursion on the split keys "by this same method" of the
-// paper's introduction: a stratified random sample of SAMPLE2 tagged keys gives
+// (k_repart) -- the introduction of the paper lets split keys be sorted again
+// with the same partitioning scheme: a stratified random sample of SAMPLE2 tagged keys gives
 // p2 - 1 splitters (tag = position inside the segment), a counting pass and a
 // stable scatter move the keys into p2 child segments in another buffer, and
 // the children go to the leaf list or to the next level's list.
