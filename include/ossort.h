@@ -184,6 +184,149 @@ int os_sort_noalloc(int key_type, const void* d_keys_in, void* d_keys_out,
                     const os_params* prm, void* stream);
 
 /*
+ * ---- Batched segmented sort -------------------------------------------------
+ * Many independent arrays held back to back in one buffer ("segments"), every
+ * one sorted on its own by one fixed sequence of persistent kernels, each of
+ * which walks the whole segment table.  (The paper sorts one array; the
+ * batched form applies its SqRan template, Algorithm 2, to every segment, with
+ * p and s chosen per length class as the paper's calibration of omega_n
+ * through n suggests.)
+ *
+ * Segment g is [off[g], off[g+1]) of the buffer; it is sorted exactly as
+ * os_sort sorts it alone with split = OS_RAN, the p and s of its length class
+ * and seed u(seed, 2, g) (output g of stream 2 of the counter-based
+ * SplitMix64 keyed by seed): the same splitters (tags are positions inside the
+ * segment), the same bucket sizes, the same output.  A segment whose class has
+ * p = 1, or that is shorter than 2 p s, is one bucket (the too-small rule of
+ * os_params).
+ *
+ * Length classes: segment g belongs to the first class k with
+ * len_g <= classes[k].max_len, or to the last class when it is longer than every
+ * max_len.  max_len must increase strictly from class to class.
+ *   p    : buckets per segment, 1 <= p <= OS_MAX_P (1: the segment is sorted
+ *          whole, directly in shared memory when it fits one CTA).
+ *   s    : random oversampling factor; p s <= OS_SEG_MAX_PS when p > 1.
+ *   tile : keys per classify / scatter tile (a CTA's unit of work), a multiple
+ *          of 2048 up to 16384.
+ */
+#define OS_SEG_MAX_CLASSES 32u
+#define OS_SEG_MAX_PS      4096u
+#define OS_SEG_MAX_NSEG    (1u << 26)
+
+typedef struct {
+    uint64_t max_len;
+    uint32_t p;
+    uint32_t s;
+    uint32_t tile;
+    uint32_t reserved;   /* must be 0 */
+} os_seg_class;
+
+/*
+ * Optional per-segment statistics, written to DEVICE arrays owned by the caller
+ * (each may be NULL) on the sort's stream, without synchronizing.
+ *   bucket_base   : [nseg + 1]: first bucket of segment g in the two arrays
+ *                   below; bucket_base[nseg] = total buckets.  Segment g has
+ *                   bucket_base[g+1] - bucket_base[g] buckets (its p, or 1).
+ *   bucket_sizes  : [bucket_cap] bucket sizes, in bucket order.
+ *   splitter_keys : [bucket_cap] keys: segment g's p - 1 splitters sit at
+ *                   bucket_base[g] .. bucket_base[g] + p - 2.
+ *   splitter_tags : [bucket_cap] their positions inside the segment.
+ *   bucket_cap    : capacity of the three bucket arrays; entries beyond it are
+ *                   not written.
+ */
+typedef struct {
+    uint32_t* bucket_base;
+    uint32_t* bucket_sizes;
+    void*     splitter_keys;
+    uint32_t* splitter_tags;
+    uint64_t  bucket_cap;
+} os_seg_stats;
+
+/*
+ * Workspace bytes os_sort_segmented needs for n keys in nseg segments with this
+ * class table.  With classes == NULL (nclass ignored): the most any table that
+ * os_tune_segmented may return can need.
+ * Errors: OS_ERR_ARG (bytes NULL, bad class table), OS_ERR_UNSUPPORTED (n above
+ * OS_MAX_N, nseg above OS_SEG_MAX_NSEG, or planned totals beyond 32 bits).
+ */
+int os_workspace_size_segmented(int key_type, uint64_t n, uint32_t nseg, int has_vals,
+                                const os_seg_class* classes, uint32_t nclass, size_t* bytes);
+
+/*
+ * Sort every segment of d_keys_in into the same range of d_keys_out.
+ *   d_keys_in     : n keys, device, read only.  Must not overlap d_keys_out.
+ *   d_keys_out    : n keys, device.
+ *   d_vals_in/out : n uint32 payloads each, or both NULL; stable order.
+ *   d_seg_offsets : nseg + 1 uint64, DEVICE: off[0] = 0, non-decreasing,
+ *                   off[nseg] = n (a violation sets an error bit in the status
+ *                   word and the offending segments are left unsorted).
+ *   classes       : HOST array of nclass length classes (read during the call).
+ *   seed          : batch seed; segment g's sample uses u(seed, 2, g).
+ *   stats         : NULL, or device arrays to fill (see os_seg_stats).
+ * Enqueues a fixed sequence of kernels whose shape depends only on n, nseg,
+ * the payload and the classes, never on the offsets (no synchronization, no
+ * host read of device data), so the call may be captured in a CUDA graph.
+ * Device-side errors are read with os_check on the same workspace.
+ */
+int os_sort_segmented(int key_type, const void* d_keys_in, void* d_keys_out,
+                      const uint32_t* d_vals_in, uint32_t* d_vals_out, uint64_t n,
+                      const uint64_t* d_seg_offsets, uint32_t nseg,
+                      const os_seg_class* classes, uint32_t nclass, uint64_t seed,
+                      void* d_ws, size_t ws_bytes, void* stream, const os_seg_stats* stats);
+
+/*
+ * CUDA graph of one os_sort_segmented call: captured once, launched many times.
+ * The graph reads the keys, payloads and offsets at the captured addresses
+ * every time it runs, so the caller may rewrite their contents between launches
+ * (any offsets with the same n and nseg).  Capture runs on a private stream
+ * and enqueues no work; os_graph_launch enqueues the whole sort on `stream`.
+ * The workspace must stay allocated and unused by other calls while the graph
+ * may run.
+ */
+typedef struct os_graph_s* os_graph;
+
+int os_graph_capture_segmented(os_graph* graph, int key_type, const void* d_keys_in, void* d_keys_out,
+                               const uint32_t* d_vals_in, uint32_t* d_vals_out, uint64_t n,
+                               const uint64_t* d_seg_offsets, uint32_t nseg,
+                               const os_seg_class* classes, uint32_t nclass, uint64_t seed,
+                               void* d_ws, size_t ws_bytes, const os_seg_stats* stats);
+int os_graph_launch(os_graph graph, void* stream);
+/* Kernels one launch of the graph runs. */
+uint64_t os_graph_kernels(os_graph graph);
+int os_graph_destroy(os_graph graph);
+
+/*
+ * Starting class table for segments up to max_len: one class of whole
+ * segments up to the shared-memory sort's capacity (8192 int32 keys, 4096
+ * 64-bit keys) with p = 1, then classes doubling in length, each with p a power
+ * of two giving buckets near 60% of that capacity and s = 16.
+ * Writes at most max_classes entries; *nclass receives the count.
+ */
+int os_seg_default_classes(int key_type, uint64_t max_len, os_seg_class* classes,
+                           uint32_t max_classes, uint32_t* nclass);
+
+/*
+ * Autotuner: times os_sort_segmented on the caller's own batch and chooses the
+ * class table (the whole-segment cutoff, and p, s and tile per length class)
+ * by coordinate descent from os_seg_default_classes: cutoff in {capacity/2,
+ * capacity, 2 capacity}; per class (largest share of keys first)
+ * p in {p/4, p/2, 2p, 4p}, s in {4, 8, 16, 32, 64}, tile in {2048, 4096, 8192},
+ * keeping a change only when it lowers the median of `reps` timed runs.
+ *   h_seg_offsets : the same offsets as d_seg_offsets, in HOST memory.
+ *   d_keys_out, d_vals_out : scratch the trial sorts write.
+ *   d_ws, ws_bytes : os_workspace_size_segmented(..., NULL, ...) bytes cover
+ *                   every candidate; candidates needing more are skipped.
+ *   classes, max_classes, nclass : the chosen table.
+ *   best_ms       : median time of the chosen table (may be NULL).
+ * Synchronizes `stream` after every trial.
+ */
+int os_tune_segmented(int key_type, const void* d_keys_in, void* d_keys_out,
+                      const uint32_t* d_vals_in, uint32_t* d_vals_out, uint64_t n,
+                      const uint64_t* d_seg_offsets, const uint64_t* h_seg_offsets, uint32_t nseg,
+                      uint64_t seed, void* d_ws, size_t ws_bytes, void* stream, uint32_t reps,
+                      os_seg_class* classes, uint32_t max_classes, uint32_t* nclass, float* best_ms);
+
+/*
  * Synchronize `stream` and read the device status word in the workspace of the
  * last sort enqueued with it: OS_OK, or OS_ERR_DEVICE with the raw error bits in
  * *bits (may be NULL).

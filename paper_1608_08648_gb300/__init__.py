@@ -11,9 +11,11 @@ from __future__ import annotations
 import ctypes
 
 from .binding import (OS_DET, OS_F64, OS_I32, OS_OK, OS_RAN, OS_STABLE, OS_U64, os_check,  # noqa: F401
+                      os_graph_capture_segmented, os_graph_destroy, os_graph_kernels, os_graph_launch,
                       os_kernel_time, os_last_cuda_error, os_launch_count, os_params, os_profile_start,
-                      os_profile_stop, os_sort, os_sort_host, os_stats, os_strerror, os_version, os_workspace_size,
-                      os_workspace_size_host)
+                      os_profile_stop, os_seg_class, os_seg_default_classes, os_seg_stats, os_sort, os_sort_host,
+                      os_sort_segmented, os_stats, os_strerror, os_tune_segmented, os_version, os_workspace_size,
+                      os_workspace_size_host, os_workspace_size_segmented)
 
 KEY_TYPES = {"i32": OS_I32, "u64": OS_U64, "f64": OS_F64}
 SPLITS = {"det": OS_DET, "ran": OS_RAN}
@@ -98,3 +100,145 @@ def sort(keys, values=None, *, split="ran", p=1024, s=16, seed=0, out=None, valu
                 "spl_keys": spl_k.view(dt)[: (p - 1 if pu > 1 else 0)], "spl_tags": spl_t[: (p - 1 if pu > 1 else 0)],
                 "bucket_sizes": sizes}
     return out, values_out, info
+
+
+# ---- batched segmented sort ---------------------------------------------------
+
+def default_classes(key_type, max_len):
+    """The library's starting class table for segments up to max_len, as
+    (max_len, p, s, tile) tuples."""
+    kt = KEY_TYPES[key_type] if isinstance(key_type, str) else int(key_type)
+    rc, cl = os_seg_default_classes(kt, int(max_len))
+    if rc != OS_OK:
+        raise OssortError(rc, "os_seg_default_classes")
+    return [(c.max_len, c.p, c.s, c.tile) for c in cl]
+
+
+def _seg_common(keys, offsets, values, key_type):
+    import torch
+    assert keys.is_cuda and keys.dim() == 1 and keys.is_contiguous()
+    assert offsets.is_cuda and offsets.dtype == torch.int64 and offsets.dim() == 1 and offsets.is_contiguous()
+    kt = _key_type(keys, key_type)
+    if values is not None:
+        assert values.is_cuda and values.numel() == keys.numel() and values.element_size() == 4
+    return kt, keys.numel(), offsets.numel() - 1
+
+
+def segmented_workspace_bytes(n, nseg, key_type="f64", has_vals=False, classes=None) -> int:
+    """Workspace of os_sort_segmented (classes None: any table the tuner may return)."""
+    kt = KEY_TYPES[key_type] if isinstance(key_type, str) else int(key_type)
+    rc, b = os_workspace_size_segmented(kt, int(n), int(nseg), has_vals, classes)
+    if rc != OS_OK:
+        raise OssortError(rc, "os_workspace_size_segmented")
+    return b
+
+
+def sort_segmented(keys, offsets, values=None, *, classes=None, seed=0, out=None, values_out=None,
+                   workspace=None, stream=None, key_type=None, stats=False):
+    """Sort every segment [offsets[g], offsets[g+1]) of a 1-D CUDA tensor on its own
+    (os_sort_segmented).  offsets: CUDA int64 tensor of nseg + 1 entries.  classes:
+    (max_len, p, s, tile) tuples; None takes default_classes for the longest segment
+    (which reads the offsets back to the host).  Returns (keys_out, values_out, stats),
+    stats a dict of CUDA tensors (bucket_base, bucket_sizes, splitter_keys,
+    splitter_tags) when requested."""
+    import torch
+    kt, n, nseg = _seg_common(keys, offsets, values, key_type)
+    if classes is None:
+        max_len = int((offsets[1:] - offsets[:-1]).max().item()) if nseg > 0 else 0
+        classes = default_classes(kt, max_len)
+    if out is None:
+        out = torch.empty_like(keys)
+    hv = values is not None
+    if hv and values_out is None:
+        values_out = torch.empty_like(values)
+    rc, need = os_workspace_size_segmented(kt, n, nseg, hv, classes)
+    if rc != OS_OK:
+        raise OssortError(rc, "os_workspace_size_segmented")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=keys.device)
+    st = stream if stream is not None else torch.cuda.current_stream(keys.device)
+    st_handle = st.cuda_stream if hasattr(st, "cuda_stream") else int(st)
+    info, so = None, None
+    if stats:
+        cap = nseg * max(int(c[1]) for c in classes) + 1
+        info = {"bucket_base": torch.zeros(nseg + 1, dtype=torch.int32, device=keys.device),
+                "bucket_sizes": torch.zeros(cap, dtype=torch.int32, device=keys.device),
+                "splitter_keys": torch.zeros(cap, dtype=keys.dtype, device=keys.device),
+                "splitter_tags": torch.zeros(cap, dtype=torch.int32, device=keys.device)}
+        so = os_seg_stats(info["bucket_base"].data_ptr(), info["bucket_sizes"].data_ptr(),
+                          info["splitter_keys"].data_ptr(), info["splitter_tags"].data_ptr(), cap)
+    rc = os_sort_segmented(kt, keys.data_ptr(), out.data_ptr(), values.data_ptr() if hv else None,
+                           values_out.data_ptr() if hv else None, n, offsets.data_ptr(), nseg, classes, seed,
+                           workspace.data_ptr(), workspace.numel(), st_handle, so)
+    if rc != OS_OK:
+        raise OssortError(rc, "os_sort_segmented")
+    return out, values_out, info
+
+
+class SegmentedGraph:
+    """A CUDA graph of one os_sort_segmented call on fixed buffers
+    (os_graph_capture_segmented); launch() replays the whole batched sort on a
+    stream.  The keys, payloads and offsets may be rewritten in place between
+    launches."""
+
+    def __init__(self, keys, offsets, out, values=None, values_out=None, *, classes, seed=0, workspace=None,
+                 key_type=None):
+        import torch
+        kt, n, nseg = _seg_common(keys, offsets, values, key_type)
+        hv = values is not None
+        rc, need = os_workspace_size_segmented(kt, n, nseg, hv, classes)
+        if rc != OS_OK:
+            raise OssortError(rc, "os_workspace_size_segmented")
+        if workspace is None or workspace.numel() < need:
+            workspace = torch.empty(need, dtype=torch.uint8, device=keys.device)
+        self._keep = (keys, offsets, out, values, values_out, workspace)
+        rc, self.handle = os_graph_capture_segmented(kt, keys.data_ptr(), out.data_ptr(),
+                                                     values.data_ptr() if hv else None,
+                                                     values_out.data_ptr() if hv else None, n, offsets.data_ptr(),
+                                                     nseg, classes, seed, workspace.data_ptr(), workspace.numel())
+        if rc != OS_OK:
+            raise OssortError(rc, "os_graph_capture_segmented")
+        self.kernels = os_graph_kernels(self.handle)
+        self.workspace = workspace
+
+    def launch(self, stream=None):
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream()
+        rc = os_graph_launch(self.handle, st.cuda_stream if hasattr(st, "cuda_stream") else int(st))
+        if rc != OS_OK:
+            raise OssortError(rc, "os_graph_launch")
+
+    def close(self):
+        if getattr(self, "handle", 0):
+            os_graph_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tune_segmented(keys, offsets, values=None, *, seed=0, reps=3, workspace=None, stream=None, key_type=None):
+    """os_tune_segmented on the caller's batch: returns (classes, best_ms), classes as
+    (max_len, p, s, tile) tuples."""
+    import numpy as np
+    import torch
+    kt, n, nseg = _seg_common(keys, offsets, values, key_type)
+    hv = values is not None
+    rc, need = os_workspace_size_segmented(kt, n, nseg, hv, None)
+    if rc != OS_OK:
+        raise OssortError(rc, "os_workspace_size_segmented")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=keys.device)
+    h_off = np.ascontiguousarray(offsets.cpu().numpy().astype(np.uint64))
+    out = torch.empty_like(keys)
+    vout = torch.empty_like(values) if hv else None
+    st = stream if stream is not None else torch.cuda.current_stream(keys.device)
+    rc, cl, ms = os_tune_segmented(kt, keys.data_ptr(), out.data_ptr(), values.data_ptr() if hv else None,
+                                   vout.data_ptr() if hv else None, n, offsets.data_ptr(), h_off.ctypes.data, nseg,
+                                   seed, workspace.data_ptr(), workspace.numel(), st.cuda_stream, reps)
+    if rc != OS_OK:
+        raise OssortError(rc, "os_tune_segmented")
+    return [(c.max_len, c.p, c.s, c.tile) for c in cl], ms

@@ -19,6 +19,9 @@ OS_MAX_N = 1 << 31
 OS_MAX_P = 4096
 OS_MAX_PS = 1 << 24
 OS_NOALLOC_SCRATCH_BYTES = 64 << 20
+OS_SEG_MAX_CLASSES = 32
+OS_SEG_MAX_PS = 4096
+OS_SEG_MAX_NSEG = 1 << 26
 
 _u32, _u64, _i32, _vp, _sz = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t
 
@@ -35,6 +38,15 @@ class os_stats(ctypes.Structure):
 class os_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", _u64), ("total_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double)]
+
+
+class os_seg_class(ctypes.Structure):
+    _fields_ = [("max_len", _u64), ("p", _u32), ("s", _u32), ("tile", _u32), ("reserved", _u32)]
+
+
+class os_seg_stats(ctypes.Structure):
+    _fields_ = [("bucket_base", _vp), ("bucket_sizes", _vp), ("splitter_keys", _vp), ("splitter_tags", _vp),
+                ("bucket_cap", _u64)]
 
 
 _lib = None
@@ -80,6 +92,27 @@ def lib() -> ctypes.CDLL:
         L.os_profile_stop.argtypes = [ctypes.POINTER(os_kernel_time), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.os_check.restype = ctypes.c_int
         L.os_check.argtypes = [_vp, _vp, ctypes.POINTER(_u32)]
+        cls_p = ctypes.POINTER(os_seg_class)
+        L.os_workspace_size_segmented.restype = ctypes.c_int
+        L.os_workspace_size_segmented.argtypes = [ctypes.c_int, _u64, _u32, ctypes.c_int, cls_p, _u32,
+                                                  ctypes.POINTER(_sz)]
+        L.os_sort_segmented.restype = ctypes.c_int
+        L.os_sort_segmented.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp, _u64, _vp, _u32, cls_p, _u32, _u64,
+                                        _vp, _sz, _vp, ctypes.POINTER(os_seg_stats)]
+        L.os_graph_capture_segmented.restype = ctypes.c_int
+        L.os_graph_capture_segmented.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _vp, _vp, _vp, _vp, _u64, _vp,
+                                                 _u32, cls_p, _u32, _u64, _vp, _sz, ctypes.POINTER(os_seg_stats)]
+        L.os_graph_launch.restype = ctypes.c_int
+        L.os_graph_launch.argtypes = [_vp, _vp]
+        L.os_graph_kernels.restype = _u64
+        L.os_graph_kernels.argtypes = [_vp]
+        L.os_graph_destroy.restype = ctypes.c_int
+        L.os_graph_destroy.argtypes = [_vp]
+        L.os_seg_default_classes.restype = ctypes.c_int
+        L.os_seg_default_classes.argtypes = [ctypes.c_int, _u64, cls_p, _u32, ctypes.POINTER(_u32)]
+        L.os_tune_segmented.restype = ctypes.c_int
+        L.os_tune_segmented.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp, _u64, _vp, _vp, _u32, _u64, _vp, _sz,
+                                        _vp, _u32, cls_p, _u32, ctypes.POINTER(_u32), ctypes.POINTER(ctypes.c_float)]
         _lib = L
     return _lib
 
@@ -148,3 +181,77 @@ def os_profile_stop(max_entries: int = 64) -> tuple[int, list[dict]]:
     out = [{"name": arr[i].name.decode(), "launches": int(arr[i].launches), "total_ms": float(arr[i].total_ms),
             "max_ms": float(arr[i].max_ms)} for i in range(min(cnt.value, max_entries))]
     return rc, out
+
+
+def _class_array(classes) -> tuple[ctypes.Array, int]:
+    """classes: a sequence of os_seg_class or of (max_len, p, s, tile) tuples."""
+    arr = (os_seg_class * max(1, len(classes)))()
+    for i, c in enumerate(classes):
+        arr[i] = c if isinstance(c, os_seg_class) else os_seg_class(int(c[0]), int(c[1]), int(c[2]), int(c[3]), 0)
+    return arr, len(classes)
+
+
+def os_workspace_size_segmented(key_type: int, n: int, nseg: int, has_vals: bool, classes) -> tuple[int, int]:
+    """classes None: the bound covering every table os_tune_segmented may return."""
+    b = _sz(0)
+    if classes is None:
+        rc = lib().os_workspace_size_segmented(key_type, n, nseg, int(bool(has_vals)), None, 0, ctypes.byref(b))
+    else:
+        arr, k = _class_array(classes)
+        rc = lib().os_workspace_size_segmented(key_type, n, nseg, int(bool(has_vals)), arr, k, ctypes.byref(b))
+    return rc, int(b.value)
+
+
+def os_sort_segmented(key_type: int, d_keys_in: int, d_keys_out: int, d_vals_in: int | None,
+                      d_vals_out: int | None, n: int, d_seg_offsets: int, nseg: int, classes, seed: int,
+                      d_ws: int, ws_bytes: int, stream: int | None, stats: os_seg_stats | None = None) -> int:
+    arr, k = _class_array(classes)
+    return lib().os_sort_segmented(key_type, d_keys_in, d_keys_out, d_vals_in, d_vals_out, n, d_seg_offsets, nseg,
+                                   arr, k, seed & ((1 << 64) - 1), d_ws, ws_bytes, stream,
+                                   ctypes.byref(stats) if stats is not None else None)
+
+
+def os_graph_capture_segmented(key_type: int, d_keys_in: int, d_keys_out: int, d_vals_in: int | None,
+                               d_vals_out: int | None, n: int, d_seg_offsets: int, nseg: int, classes, seed: int,
+                               d_ws: int, ws_bytes: int, stats: os_seg_stats | None = None) -> tuple[int, int]:
+    """Returns (status, graph handle)."""
+    h = _vp(None)
+    arr, k = _class_array(classes)
+    rc = lib().os_graph_capture_segmented(ctypes.byref(h), key_type, d_keys_in, d_keys_out, d_vals_in, d_vals_out,
+                                          n, d_seg_offsets, nseg, arr, k, seed & ((1 << 64) - 1), d_ws, ws_bytes,
+                                          ctypes.byref(stats) if stats is not None else None)
+    return rc, (h.value or 0)
+
+
+def os_graph_launch(graph: int, stream: int | None) -> int:
+    return lib().os_graph_launch(graph, stream)
+
+
+def os_graph_kernels(graph: int) -> int:
+    return int(lib().os_graph_kernels(graph))
+
+
+def os_graph_destroy(graph: int) -> int:
+    return lib().os_graph_destroy(graph)
+
+
+def os_seg_default_classes(key_type: int, max_len: int, max_classes: int = OS_SEG_MAX_CLASSES):
+    """Returns (status, [os_seg_class, ...])."""
+    arr = (os_seg_class * max_classes)()
+    k = _u32(0)
+    rc = lib().os_seg_default_classes(key_type, max_len, arr, max_classes, ctypes.byref(k))
+    return rc, [arr[i] for i in range(k.value)]
+
+
+def os_tune_segmented(key_type: int, d_keys_in: int, d_keys_out: int, d_vals_in: int | None,
+                      d_vals_out: int | None, n: int, d_seg_offsets: int, h_seg_offsets: int, nseg: int, seed: int,
+                      d_ws: int, ws_bytes: int, stream: int | None, reps: int = 3,
+                      max_classes: int = OS_SEG_MAX_CLASSES):
+    """Returns (status, [os_seg_class, ...], best_ms)."""
+    arr = (os_seg_class * max_classes)()
+    k = _u32(0)
+    ms = ctypes.c_float(0.0)
+    rc = lib().os_tune_segmented(key_type, d_keys_in, d_keys_out, d_vals_in, d_vals_out, n, d_seg_offsets,
+                                 h_seg_offsets, nseg, seed & ((1 << 64) - 1), d_ws, ws_bytes, stream, reps, arr,
+                                 max_classes, ctypes.byref(k), ctypes.byref(ms))
+    return rc, [arr[i] for i in range(k.value)], float(ms.value)

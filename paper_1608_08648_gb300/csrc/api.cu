@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/ossort.h"
+#include "api_util.h"
 #include "driver.cuh"
 
 using namespace ossort;
@@ -40,7 +41,15 @@ cudaEvent_t pool_event() {
 }  // namespace
 
 namespace ossort {
+// A launch enqueued while its stream is being captured into a graph runs only
+// when the graph is launched: it is counted then (add_launches), not here.
+static bool capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+void add_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 void prof_before(cudaStream_t st, const char* name) {
+    if (capturing(st)) return;
     g_launches.fetch_add(1, std::memory_order_relaxed);
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_prof_on) return;
@@ -53,6 +62,7 @@ void prof_after(cudaStream_t st, const char* name) {
         const char* e = std::getenv("OSSORT_DEBUG_SYNC");
         return e && e[0] == '1';
     }();
+    if (capturing(st)) return;
     if (debug_sync) {
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -69,13 +79,24 @@ void prof_after(cudaStream_t st, const char* name) {
 }  // namespace ossort
 
 namespace {
-
 thread_local int g_last_cuda = 0;
+}  // namespace
 
+namespace ossort {
 int cuda_fail(cudaError_t e) {
     g_last_cuda = (int)e;
     return OS_ERR_CUDA;
 }
+
+int num_sms_of_current_device() {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaGetLastError();
+    return sms > 0 ? sms : 152;
+}
+}  // namespace ossort
+
+namespace {
 
 size_t key_bytes(int kt) { return kt == OS_I32 ? 4 : 8; }
 
@@ -95,13 +116,6 @@ int dispatch(int kt, RunArgs& a) {
         case OS_U64: return run_u64(a);
         default: return run_f64(a);
     }
-}
-
-int num_sms_of_current_device() {
-    int dev = 0, sms = 152;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaGetLastError();
-    return sms > 0 ? sms : 152;
 }
 
 size_t plan_bytes(int kt, uint64_t n, bool has_vals, const os_params* prm) {

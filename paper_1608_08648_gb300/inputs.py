@@ -43,6 +43,7 @@ S_KEY64 = 74
 S_EDGE_KIND = 81
 S_EDGE_BITS = 82
 S_PAYLOAD = 91
+S_SEGLEN = 101
 
 DISTRIBUTIONS = ("uniform", "gaussian", "zero", "bucket", "staggered", "ggroup", "dup")
 
@@ -219,3 +220,40 @@ def edge_f64_keys(n: int, seed: int = 7, start: int = 0, count: int | None = Non
 def payload_index(n: int, start: int = 0, count: int | None = None, device="cpu") -> torch.Tensor:
     """The u32 payload 'original index' (held in an int32 tensor)."""
     return _positions(n, start, count, device).to(torch.int32)
+
+
+def segment_lengths(nseg: int, lo: int = 1024, hi: int = 4194304, cap: int = 1 << 28,
+                    seed: int = 3) -> tuple[torch.Tensor, float]:
+    """Lengths of a batch of nseg arrays, log-uniform in [lo, hi): L_g = floor(lo *
+    (hi/lo)^u_g), u_g the top 53 bits of u(seed, S_SEGLEN, g) as a unit double.
+
+    When their total exceeds ``cap`` they are compressed in log space,
+    L'_g = floor(lo * (L_g / lo)^gamma), with gamma the largest value in [0, 1]
+    (60 bisection steps) whose total is <= cap; the spread of lengths shrinks
+    but every length stays >= lo and the batch keeps nseg arrays.
+    Returns (int64 lengths on the CPU, gamma)."""
+    g = torch.arange(nseg, dtype=torch.int64)
+    u = _unit(seed, S_SEGLEN, g)
+    L = torch.floor(lo * torch.pow(torch.tensor(hi / lo, dtype=torch.float64), u))
+    ratio = L / lo
+
+    def lengths(gamma: float) -> torch.Tensor:
+        return torch.floor(lo * torch.pow(ratio, gamma)).to(torch.int64)
+
+    if int(L.sum().item()) <= cap:
+        return L.to(torch.int64), 1.0
+    a, b = 0.0, 1.0
+    for _ in range(60):
+        m = 0.5 * (a + b)
+        if int(lengths(m).sum().item()) <= cap:
+            a = m
+        else:
+            b = m
+    return lengths(a), a
+
+
+def segment_offsets(lengths: torch.Tensor) -> torch.Tensor:
+    """Offsets [0, L_0, L_0 + L_1, ...] (int64, nseg + 1 entries)."""
+    off = torch.zeros(lengths.numel() + 1, dtype=torch.int64)
+    off[1:] = torch.cumsum(lengths.to(torch.int64), 0)
+    return off
