@@ -47,6 +47,13 @@ def parse():
     ap.add_argument("--ref-sample", type=int, default=1 << 20, help="keys per step of --impl reference")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="sort", choices=["sort", "batched"],
+                    help="sort: one array (the headline line, with a 'batched' summary); batched: the "
+                         "batched segmented workload as the line's own metric")
+    ap.add_argument("--no-batched", action="store_true", help="leave the batched summary out of the sort line")
+    ap.add_argument("--segments", type=int, default=10000)
+    ap.add_argument("--no-tune", action="store_true", help="batched: the default class table, not tuned")
+    ap.add_argument("--plain-steps", type=int, default=2, help="batched: timed steps of the per-array loop")
     return ap.parse_args()
 
 
@@ -185,6 +192,224 @@ def algorithmic_bytes(name: str, n: int, kb: int, vb: int, repart_keys: int) -> 
     if name == "k_repart":
         return repart_keys * (2 * kb + vb) + repart_keys * (kb + vb)
     return 0
+
+
+# ---- batched segmented workload ------------------------------------------------------
+
+BATCH = {"nseg": 10000, "lo": 1024, "hi": 4194304, "cap": 1 << 28, "seed": 3, "dtype": "f64", "dist": "gaussian"}
+
+
+def batched_workload_name(nseg):
+    return (f"{nseg} float64 Gaussian arrays, lengths log-uniform in [2^10, 2^22] compressed to 2^28 keys "
+            f"in total, seed 3, SqRan per array, one CUDA graph launch per batch")
+
+
+def seg_alg_bytes(name, n, n_part, kb, repart_keys):
+    """Bytes a kernel of the batched sort must move per batch: classify reads the keys
+    of partitioned arrays, scatter reads and writes them, the leaf sort reads and
+    writes every key, a repartition level reads twice and writes once."""
+    if name == "k_seg_classify":
+        return n_part * kb
+    if name == "k_seg_scatter":
+        return 2 * n_part * kb
+    if name == "k_leaf":
+        return 2 * n * kb
+    if name == "k_repart":
+        return 3 * repart_keys * kb
+    return 0
+
+
+def run_batched(a, rank, world, local, steps, warmup, plain_steps):
+    """The batched workload on this GPU: the tuned (or default) class table, the
+    captured graph timed over `steps` launches, the per-array os_sort loop over the
+    same arrays, an end-to-end variant with host copies, and per-kernel times of one
+    profiled (uncaptured) call."""
+    import numpy as np
+    import torch
+
+    import paper_1608_08648_gb300 as oss
+    from paper_1608_08648_gb300 import inputs
+
+    dev = torch.device("cuda", local)
+    kt_name = BATCH["dtype"]
+    kt = oss.KEY_TYPES[kt_name]
+    kb = KEY_BYTES[kt_name]
+    L, gamma = inputs.segment_lengths(a.segments, BATCH["lo"], BATCH["hi"], BATCH["cap"], seed=BATCH["seed"])
+    off = inputs.segment_offsets(L)
+    n = int(off[-1])
+    nseg = L.numel()
+    seed = BATCH["seed"]
+    keys = inputs.keys(BATCH["dist"], n, kt_name, seed=seed + rank, device=dev)
+    d_off = off.to(dev)
+    out = torch.empty_like(keys)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+
+    t_tune = 0.0
+    if a.no_tune:
+        classes = oss.default_classes(kt_name, int(L.max()))
+        tune_ms = None
+    else:
+        t0 = time.perf_counter()
+        classes, tune_ms = oss.tune_segmented(keys, d_off, seed=seed, reps=2)
+        t_tune = time.perf_counter() - t0
+    g = oss.SegmentedGraph(keys, d_off, out, classes=classes, seed=seed)
+    for _ in range(warmup):
+        g.launch(stream)
+    rc, ctr = oss.os_read_counters(g.workspace.data_ptr(), sh)
+    assert rc == 0 and ctr["errors"] == 0, f"device status {ctr}"
+    # correctness of the warm-up output (not timed): sorted inside every array, a permutation of it
+    lens = d_off[1:] - d_off[:-1]
+    seg = torch.repeat_interleave(torch.arange(nseg, device=dev), lens)
+    b = keys.view(torch.int64)
+    ok = torch.where(b < 0, b ^ torch.iinfo(torch.int64).max, b)
+    p1 = torch.sort(ok, stable=True).indices
+    perm = p1[torch.sort(seg[p1], stable=True).indices]
+    assert torch.equal(out.view(torch.int64), keys.view(torch.int64)[perm]), "batched output wrong"
+    del seg, ok, p1, perm
+
+    clocks = Clocks(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = oss.os_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        g.launch(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = oss.os_launch_count() - launches0
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, world)
+
+    # per-array plain launches: os_sort on every array with its class's p and s and the
+    # array's own seed (so the outputs must equal the batched ones)
+    seeds = (inputs.u64(seed, 2, torch.arange(nseg, dtype=torch.int64))).tolist()
+    offs = off.tolist()
+    calls, need_max = [], 0
+    for gi in range(nseg):
+        ln = offs[gi + 1] - offs[gi]
+        k = next((i for i, c in enumerate(classes) if ln <= c[0]), len(classes) - 1)
+        prm = oss.params("ran", classes[k][1], classes[k][2], seeds[gi] & ((1 << 64) - 1))
+        rc, need = oss.os_workspace_size(kt, ln, False, prm)
+        assert rc == 0
+        need_max = max(need_max, need)
+        calls.append((keys.data_ptr() + offs[gi] * kb, ln, prm))
+    out_plain = torch.empty_like(keys)
+    wsp = torch.empty(need_max, dtype=torch.uint8, device=dev)
+
+    def plain_step():
+        base_out = out_plain.data_ptr() - keys.data_ptr()
+        for kin, ln, prm in calls:
+            r = oss.os_sort(kt, kin, kin + base_out, None, None, ln, prm, wsp.data_ptr(), need_max, sh, None)
+            if r != 0:
+                raise RuntimeError(f"os_sort failed: {oss.os_strerror(r)}")
+
+    plain_step()
+    torch.cuda.synchronize()
+    assert torch.equal(out_plain.view(torch.int64), out.view(torch.int64)), "per-array output differs"
+    barrier(world)
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1e = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(plain_steps):
+        plain_step()
+    p1e.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = max_over_ranks(p0.elapsed_time(p1e) / plain_steps, world)
+    del wsp, out_plain
+
+    # end to end: pinned host keys and offsets in, sorted keys out, graph in between
+    e2e = None
+    if not a.no_e2e:
+        h_keys = keys.cpu().pin_memory()
+        h_off = off.pin_memory()
+        h_out = torch.empty_like(h_keys).pin_memory()
+
+        def e2e_step():
+            keys.copy_(h_keys, non_blocking=True)
+            d_off.copy_(h_off, non_blocking=True)
+            g.launch(stream)
+            h_out.copy_(out, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        k2 = max(2, min(steps, 5))
+        for _ in range(k2):
+            e2e_step()
+        torch.cuda.synchronize()
+        t = max_over_ranks((time.perf_counter() - t0) / k2, world)
+        assert torch.equal(h_out.view(torch.int64), out.cpu().view(torch.int64))
+        e2e = {"value": world * n / t, "unit": "keys/s", "ms_per_step": t * 1e3,
+               "h2d_bytes_per_step": n * kb + (nseg + 1) * 8, "d2h_bytes_per_step": n * kb}
+
+    # per-kernel device times of one uncaptured call (events around every launch)
+    ws2 = g.workspace
+    oss.os_profile_start()
+    rc = oss.os_sort_segmented(kt, keys.data_ptr(), out.data_ptr(), None, None, n, d_off.data_ptr(), nseg, classes,
+                               seed, ws2.data_ptr(), ws2.numel(), sh)
+    assert rc == 0
+    rc, prof = oss.os_profile_stop()
+    rc, ctr = oss.os_read_counters(ws2.data_ptr(), sh)
+    n_part = 0                      # keys of the arrays that are partitioned (p > 1 after the small rule)
+    for x in L.tolist():
+        c = classes[next((i for i, c in enumerate(classes) if x <= c[0]), len(classes) - 1)]
+        if c[1] > 1 and x >= 2 * c[1] * c[2]:
+            n_part += x
+    peaks, peak_kind = measured_peaks()
+    dom = max(prof, key=lambda k: k["total_ms"])
+    alg = seg_alg_bytes(dom["name"], n, n_part, kb, ctr["repart_keys"])
+    achieved = alg / (dom["total_ms"] / 1e3) / 1e9 if dom["total_ms"] > 0 else 0.0
+    roof = {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1), "peak": float(peaks["hbm_gbs"]),
+            "unit": "GB/s", "frac": round(achieved / float(peaks["hbm_gbs"]), 4), "traffic": None,
+            "peak_source": f"{peak_kind} hbm_gbs", "avg_launch_ms": round(dom["total_ms"] / dom["launches"], 4),
+            "alg_bytes_per_step": alg}
+    g.close()
+    return {"n": n, "nseg": nseg, "gamma": round(gamma, 6), "max_len": int(L.max()), "ms": ms,
+            "value": world * n / (ms / 1e3), "plain_ms": plain_ms, "plain_value": world * n / (plain_ms / 1e3),
+            "speedup_vs_plain": plain_ms / ms, "classes": [list(map(int, c)) for c in classes],
+            "tuned": not a.no_tune, "tune_s": round(t_tune, 2), "tune_best_ms": tune_ms,
+            "graph_kernels": g.kernels, "gpu_launches": launches, "clocks": clk, "e2e": e2e, "roofline": roof,
+            "kernels": [{"name": k["name"], "launches": k["launches"], "total_ms": round(k["total_ms"], 4),
+                         "share": round(k["total_ms"] / max(1e-9, sum(x["total_ms"] for x in prof)), 4)}
+                        for k in sorted(prof, key=lambda k: -k["total_ms"])],
+            "repart_keys": ctr["repart_keys"], "depth": ctr["depth"], "partitioned_keys": n_part}
+
+
+def cpu_baseline_batched(a, max_keys=1 << 23):
+    """The oracle, single-threaded, on the first arrays of the batched workload (whole
+    arrays, about max_keys keys), each with its class's p, s and seed."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1608_08648_gb300 as oss
+    from paper_1608_08648_gb300 import inputs
+    L, _ = inputs.segment_lengths(a.segments, BATCH["lo"], BATCH["hi"], BATCH["cap"], seed=BATCH["seed"])
+    lens = L.tolist()
+    m, cnt = 0, 0
+    while cnt < len(lens) and m + lens[cnt] <= max_keys:
+        m += lens[cnt]
+        cnt += 1
+    keys = inputs.keys(BATCH["dist"], int(L.sum()), "f64", seed=BATCH["seed"], count=m).numpy()
+    classes = oss.default_classes("f64", int(L.max()))
+    seeds = inputs.u64(BATCH["seed"], 2, torch.arange(cnt, dtype=torch.int64)).tolist()
+    t0 = time.perf_counter()
+    pos = 0
+    for gi in range(cnt):
+        ln = lens[gi]
+        k = next((i for i, c in enumerate(classes) if ln <= c[0]), len(classes) - 1)
+        oracle.sort(keys[pos:pos + ln], "f64", "ran", classes[k][1], classes[k][2], seed=seeds[gi] & ((1 << 64) - 1))
+        pos += ln
+    t = time.perf_counter() - t0
+    return {"value": m / t, "unit": "keys/s", "cores": 1, "kind": "oracle", "host_cores": cpu_cores(),
+            "sample": f"first {cnt} arrays ({m} keys) of the batched workload, one oracle run each ({t:.2f} s)"}
 
 
 # ---- our arm ------------------------------------------------------------------------
@@ -327,6 +552,39 @@ def run_ours(a, rank, world, local):
                        "note": "torch.sort of the same keys (radix sort returning values and indices), not a baseline"}}
     if rank == 0 and world == 1 and not a.no_cpu:
         res["cpu_baseline"] = cpu_baseline(a)
+    if not a.no_batched:
+        del keys, out, tk
+        torch.cuda.empty_cache()
+        bt = run_batched(a, rank, world, local, steps=max(3, min(a.steps, 10)), warmup=3,
+                         plain_steps=a.plain_steps)
+        res["batched"] = {"workload": batched_workload_name(bt["nseg"]), "value": bt["value"], "unit": "keys/s",
+                          "ms_per_step": bt["ms"], "plain_value": bt["plain_value"], "plain_ms": bt["plain_ms"],
+                          "speedup_vs_plain": bt["speedup_vs_plain"], "classes": bt["classes"],
+                          "tuned": bt["tuned"], "e2e": bt["e2e"], "roofline": bt["roofline"],
+                          "gpu_launches": bt["gpu_launches"], "graph_kernels": bt["graph_kernels"]}
+    return res
+
+
+def run_batched_line(a, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    bt = run_batched(a, rank, world, local, steps=a.steps, warmup=a.warmup, plain_steps=a.plain_steps)
+    res = {"metric": "keys/s (batched segmented sort)", "value": bt["value"], "unit": "keys/s", "n_gpus": world,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": bt["ms"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": batched_workload_name(bt["nseg"]), "n": bt["n"], "arrays": bt["nseg"],
+                      "gamma": bt["gamma"], "max_len": bt["max_len"], "classes": bt["classes"],
+                      "tuned": bt["tuned"], "tune_s": bt["tune_s"], "graph_kernels": bt["graph_kernels"],
+                      "l2": "inputs larger than L2 (no flush needed)", "parallelism": "replicas"},
+           "roofline": bt["roofline"], "e2e": bt["e2e"], "gpu_launches": bt["gpu_launches"], "clocks": bt["clocks"],
+           "plain": {"value": bt["plain_value"], "ms_per_step": bt["plain_ms"],
+                     "speedup_of_batched": bt["speedup_vs_plain"],
+                     "note": "os_sort called once per array from Python, same classes and seeds"},
+           "kernels": bt["kernels"],
+           "stats": {"repart_keys": bt["repart_keys"], "depth": bt["depth"],
+                     "partitioned_keys": bt["partitioned_keys"]}}
+    if rank == 0 and world == 1 and not a.no_cpu:
+        res["cpu_baseline"] = cpu_baseline_batched(a)
     return res
 
 
@@ -364,6 +622,21 @@ def run_reference(a, rank, world):
     from paper_1608_08648_gb300 import inputs
     if rank != 0:
         return None
+    if a.workload == "batched":
+        cb = None
+        for _ in range(a.warmup):
+            cpu_baseline_batched(a, max_keys=a.ref_sample)
+        vals = [cpu_baseline_batched(a, max_keys=a.ref_sample) for _ in range(a.steps)]
+        v = statistics.median(x["value"] for x in vals)
+        cb = dict(vals[0], value=v)
+        return {"impl": "reference", "metric": "keys/s (batched segmented sort)", "value": v, "unit": "keys/s",
+                "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+                "ms_per_step": statistics.median(float(x["sample"].split("(")[-1].split(" s")[0]) for x in vals) * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": batched_workload_name(a.segments), "arrays": a.segments,
+                                                "parallelism": "replicas"},
+                "cpu_baseline": cb,
+                "e2e": {"value": v, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     m = min(a.ref_sample, a.keys)
     keys = inputs.keys(a.dist, a.keys, a.dtype, seed=a.seed, p=a.p, count=m).numpy()
     if a.dtype == "u64":
@@ -388,14 +661,14 @@ def run_reference(a, rank, world):
 def main():
     a = parse()
     rank, world, local = dist_setup()
+    from paper_1608_08648_gb300 import build as b
+    if rank == 0:
+        b.build()          # the batched reference arm takes its class table from the library's host code
+    barrier(world)
     if a.impl == "reference":
         res = run_reference(a, rank, world)
     else:
-        from paper_1608_08648_gb300 import build as b
-        if rank == 0:
-            b.build()
-        barrier(world)
-        res = run_ours(a, rank, world, local)
+        res = run_batched_line(a, rank, world, local) if a.workload == "batched" else run_ours(a, rank, world, local)
     if rank == 0 and res is not None:
         print(json.dumps(res), flush=True)
     if world > 1:

@@ -334,6 +334,24 @@ int os_tune_segmented(int key_type, const void* d_keys_in, void* d_keys_out,
 int os_check(const void* d_ws, void* stream, uint32_t* bits);
 
 /*
+ * Counters of the last sort (plain or segmented) enqueued with this workspace,
+ * read after synchronizing `stream`:
+ *   errors      : the device error bits (0 when none; os_check's word).
+ *   depth       : deepest in-bucket repartition level used.
+ *   repart_keys : keys moved by in-bucket repartitions, summed over levels.
+ *   bad_site, bad_index : first failed range check (0 when none).
+ */
+typedef struct {
+    uint32_t errors;
+    uint32_t depth;
+    uint64_t repart_keys;
+    uint32_t bad_site;
+    uint32_t bad_index;
+} os_counters;
+
+int os_read_counters(const void* d_ws, void* stream, os_counters* counters);
+
+/*
  * Launch accounting (Section 3 of the paper times whole runs; the library also
  * reports where device time goes).  os_launch_count returns the number of
  * kernels this library has launched in the process.  Between os_profile_start

@@ -13,7 +13,8 @@ import ctypes
 from .binding import (OS_DET, OS_F64, OS_I32, OS_OK, OS_RAN, OS_STABLE, OS_U64, os_check,  # noqa: F401
                       os_graph_capture_segmented, os_graph_destroy, os_graph_kernels, os_graph_launch,
                       os_kernel_time, os_last_cuda_error, os_launch_count, os_params, os_profile_start,
-                      os_profile_stop, os_seg_class, os_seg_default_classes, os_seg_stats, os_sort, os_sort_host,
+                      os_profile_stop, os_read_counters, os_seg_class, os_seg_default_classes, os_seg_stats,
+                      os_sort, os_sort_host,
                       os_sort_segmented, os_stats, os_strerror, os_tune_segmented, os_version, os_workspace_size,
                       os_workspace_size_host, os_workspace_size_segmented)
 

@@ -35,6 +35,11 @@ class os_stats(ctypes.Structure):
                 ("splitter_keys", _vp), ("splitter_tags", _vp), ("bucket_sizes", _vp)]
 
 
+class os_counters(ctypes.Structure):
+    _fields_ = [("errors", _u32), ("depth", _u32), ("repart_keys", _u64), ("bad_site", _u32),
+                ("bad_index", _u32)]
+
+
 class os_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", _u64), ("total_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double)]
@@ -92,6 +97,8 @@ def lib() -> ctypes.CDLL:
         L.os_profile_stop.argtypes = [ctypes.POINTER(os_kernel_time), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.os_check.restype = ctypes.c_int
         L.os_check.argtypes = [_vp, _vp, ctypes.POINTER(_u32)]
+        L.os_read_counters.restype = ctypes.c_int
+        L.os_read_counters.argtypes = [_vp, _vp, ctypes.POINTER(os_counters)]
         cls_p = ctypes.POINTER(os_seg_class)
         L.os_workspace_size_segmented.restype = ctypes.c_int
         L.os_workspace_size_segmented.argtypes = [ctypes.c_int, _u64, _u32, ctypes.c_int, cls_p, _u32,
@@ -164,6 +171,13 @@ def os_check(d_ws: int, stream: int | None) -> tuple[int, int]:
     bits = _u32(0)
     rc = lib().os_check(d_ws, stream, ctypes.byref(bits))
     return rc, int(bits.value)
+
+
+def os_read_counters(d_ws: int, stream: int | None) -> tuple[int, dict]:
+    c = os_counters()
+    rc = lib().os_read_counters(d_ws, stream, ctypes.byref(c))
+    return rc, {"errors": int(c.errors), "depth": int(c.depth), "repart_keys": int(c.repart_keys),
+                "bad_site": int(c.bad_site), "bad_index": int(c.bad_index)}
 
 
 def os_launch_count() -> int:

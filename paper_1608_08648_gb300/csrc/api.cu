@@ -347,4 +347,19 @@ int os_check(const void* d_ws, void* stream, uint32_t* bits) {
     return word ? OS_ERR_DEVICE : OS_OK;
 }
 
+int os_read_counters(const void* d_ws, void* stream, os_counters* counters) {
+    if (!d_ws || !counters) return OS_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e);
+    uint32_t w[8];
+    e = cudaMemcpy(w, d_ws, sizeof w, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    counters->errors = w[0];
+    counters->depth = w[1];
+    counters->repart_keys = (uint64_t)w[4] | ((uint64_t)w[5] << 32);
+    counters->bad_site = w[6];
+    counters->bad_index = w[7];
+    return OS_OK;
+}
+
 }  // extern "C"
