@@ -327,6 +327,97 @@ int os_tune_segmented(int key_type, const void* d_keys_in, void* d_keys_out,
                       os_seg_class* classes, uint32_t max_classes, uint32_t* nclass, float* best_ms);
 
 /*
+ * ---- Serving loop ------------------------------------------------------------
+ * A sort server for requests that arrive over time (an addition of this
+ * library; the paper sorts one array at a time).  The caller gives it one
+ * device arena -- the HBM budget -- and it keeps every request's output and
+ * workspace (splitters, buckets, work lists) inside it.  A dispatcher thread
+ * admits queued requests in arrival order as soon as an in-flight slot is free
+ * and the arena holds the request's output plus workspace, and enqueues each
+ * admitted sort (os_sort with the request's parameters) on one of several CUDA
+ * streams, so requests that arrive while others run overlap on the GPU.  A
+ * stream callback marks the request done, time-stamps it and returns its
+ * workspace to the arena at once; its output stays until os_server_release.
+ * Results are bit-identical to os_sort of the same request alone.
+ */
+typedef struct os_server_s* os_server;
+
+typedef struct {
+    void*    d_arena;       /* device memory the server sub-allocates: the HBM budget */
+    size_t   arena_bytes;
+    uint32_t streams;       /* CUDA streams the admitted sorts are spread over, 1..64 */
+    uint32_t max_inflight;  /* admitted, unfinished requests at most, >= 1 */
+} os_server_config;
+
+typedef struct {
+    int32_t     key_type;
+    uint32_t    reserved;   /* must be 0 */
+    const void* d_keys_in;  /* n device keys, resident, outside the arena; read until the request is done */
+    uint64_t    n;
+    os_params   prm;
+} os_request;
+
+typedef struct {
+    uint64_t ticket;
+    int32_t  status;        /* OS_OK, or the error of the request's sort */
+    uint32_t stream;        /* stream index the sort ran on */
+    void*    d_keys_out;    /* sorted keys inside the arena, valid until os_server_release */
+    uint64_t n;
+    uint64_t bytes;         /* arena bytes the request held while running (output + workspace) */
+    double   submit_s;      /* host steady-clock times, seconds */
+    double   admit_s;
+    double   done_s;
+} os_result;
+
+typedef struct {
+    uint64_t submitted, admitted, completed, released;
+    uint32_t queued, inflight;
+    uint64_t arena_in_use, arena_peak, arena_bytes;
+    uint32_t max_inflight_seen;
+} os_server_stats;
+
+/*
+ * Create a server on the current device.  Errors: OS_ERR_ARG (NULL arena,
+ * streams or max_inflight out of range), OS_ERR_CUDA.
+ */
+int os_server_create(const os_server_config* cfg, os_server* server);
+
+/*
+ * Queue one request; *ticket identifies it.  Never blocks on the GPU.
+ * Errors: OS_ERR_ARG (bad request), OS_ERR_UNSUPPORTED (its output plus
+ * workspace exceed the whole arena: it could never be admitted).
+ */
+int os_server_submit(os_server server, const os_request* req, uint64_t* ticket);
+
+/*
+ * Completed requests not returned before, oldest completion first: up to
+ * max_results into `results`, *count receives how many.  With timeout_us > 0
+ * waits up to that long for at least one completion.
+ */
+int os_server_poll(os_server server, os_result* results, uint32_t max_results, int64_t timeout_us,
+                   uint32_t* count);
+
+/* Return a completed request's output to the arena (after the caller used it). */
+int os_server_release(os_server server, uint64_t ticket);
+
+int os_server_get_stats(os_server server, os_server_stats* stats);
+
+/*
+ * Open-loop replay of a request trace (benchmarking): request i is submitted at
+ * arrival_s[i] seconds after the call starts (non-decreasing), completions are
+ * collected and released at once, and results[i] receives request i's record
+ * (d_keys_out is no longer valid).  Returns when every request is done.
+ */
+int os_server_replay(os_server server, const os_request* reqs, const double* arrival_s, uint32_t count,
+                     os_result* results);
+
+/*
+ * Stop the dispatcher, wait for in-flight sorts and free the server.  Queued
+ * requests that were never admitted are dropped.
+ */
+int os_server_destroy(os_server server);
+
+/*
  * Synchronize `stream` and read the device status word in the workspace of the
  * last sort enqueued with it: OS_OK, or OS_ERR_DEVICE with the raw error bits in
  * *bits (may be NULL).

@@ -243,3 +243,82 @@ def tune_segmented(keys, offsets, values=None, *, seed=0, reps=3, workspace=None
     if rc != OS_OK:
         raise OssortError(rc, "os_tune_segmented")
     return [(c.max_len, c.p, c.s, c.tile) for c in cl], ms
+
+
+# ---- serving loop -----------------------------------------------------------------
+
+class Server:
+    """A sort server over one device arena (os_server_*).  submit() takes a resident
+    CUDA tensor of keys; poll() returns finished requests with their sorted keys as a
+    tensor view into the arena, valid until release(ticket)."""
+
+    def __init__(self, arena_bytes, streams=8, max_inflight=64, device=None):
+        import torch
+        from . import binding as _b
+        self._b = _b
+        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=device or "cuda")
+        rc, self.handle = _b.os_server_create(self.arena.data_ptr(), self.arena.numel(), streams, max_inflight)
+        if rc != OS_OK:
+            raise OssortError(rc, "os_server_create")
+        self._inputs = {}      # ticket -> (input tensor, dtype): kept alive while the request may read it
+
+    def request(self, keys, split="ran", p=1024, s=16, seed=0, key_type=None):
+        kt = _key_type(keys, key_type)
+        return self._b.os_request(kt, 0, keys.data_ptr(), keys.numel(), params(split, p, s, seed))
+
+    def submit(self, keys, split="ran", p=1024, s=16, seed=0, key_type=None):
+        assert keys.is_cuda and keys.dim() == 1 and keys.is_contiguous()
+        rc, t = self._b.os_server_submit(self.handle, self.request(keys, split, p, s, seed, key_type))
+        if rc != OS_OK:
+            raise OssortError(rc, "os_server_submit")
+        self._inputs[t] = (keys, keys.dtype)
+        return t
+
+    def poll(self, max_results=64, timeout_us=0):
+        """[(ticket, status, output tensor, record)] of newly finished requests."""
+        rc, res = self._b.os_server_poll(self.handle, max_results, timeout_us)
+        if rc != OS_OK:
+            raise OssortError(rc, "os_server_poll")
+        out = []
+        for r in res:
+            keys, dt = self._inputs.pop(r.ticket, (None, None))
+            view = None
+            if keys is not None and r.status == OS_OK:
+                off = r.d_keys_out - self.arena.data_ptr()
+                view = self.arena[off:off + r.n * keys.element_size()].view(dt)
+            out.append((r.ticket, r.status, view, r))
+        return out
+
+    def release(self, ticket):
+        rc = self._b.os_server_release(self.handle, ticket)
+        if rc != OS_OK:
+            raise OssortError(rc, "os_server_release")
+
+    def stats(self):
+        rc, st = self._b.os_server_get_stats(self.handle)
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def replay(self, requests, arrival_s):
+        """Open-loop replay (os_server_replay): request i is submitted arrival_s[i]
+        seconds after the start; returns the os_result records in request order."""
+        rc, res = self._b.os_server_replay(self.handle, requests, arrival_s)
+        if rc != OS_OK:
+            raise OssortError(rc, "os_server_replay")
+        return res
+
+    def close(self):
+        if getattr(self, "handle", 0):
+            self._b.os_server_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -54,6 +54,26 @@ class os_seg_stats(ctypes.Structure):
                 ("bucket_cap", _u64)]
 
 
+class os_server_config(ctypes.Structure):
+    _fields_ = [("d_arena", _vp), ("arena_bytes", _sz), ("streams", _u32), ("max_inflight", _u32)]
+
+
+class os_request(ctypes.Structure):
+    _fields_ = [("key_type", _i32), ("reserved", _u32), ("d_keys_in", _vp), ("n", _u64), ("prm", os_params)]
+
+
+class os_result(ctypes.Structure):
+    _fields_ = [("ticket", _u64), ("status", _i32), ("stream", _u32), ("d_keys_out", _vp), ("n", _u64),
+                ("bytes", _u64), ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("done_s", ctypes.c_double)]
+
+
+class os_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", _u64), ("admitted", _u64), ("completed", _u64), ("released", _u64),
+                ("queued", _u32), ("inflight", _u32), ("arena_in_use", _u64), ("arena_peak", _u64),
+                ("arena_bytes", _u64), ("max_inflight_seen", _u32)]
+
+
 _lib = None
 
 
@@ -97,6 +117,21 @@ def lib() -> ctypes.CDLL:
         L.os_profile_stop.argtypes = [ctypes.POINTER(os_kernel_time), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.os_check.restype = ctypes.c_int
         L.os_check.argtypes = [_vp, _vp, ctypes.POINTER(_u32)]
+        L.os_server_create.restype = ctypes.c_int
+        L.os_server_create.argtypes = [ctypes.POINTER(os_server_config), ctypes.POINTER(_vp)]
+        L.os_server_submit.restype = ctypes.c_int
+        L.os_server_submit.argtypes = [_vp, ctypes.POINTER(os_request), ctypes.POINTER(_u64)]
+        L.os_server_poll.restype = ctypes.c_int
+        L.os_server_poll.argtypes = [_vp, ctypes.POINTER(os_result), _u32, ctypes.c_int64, ctypes.POINTER(_u32)]
+        L.os_server_release.restype = ctypes.c_int
+        L.os_server_release.argtypes = [_vp, _u64]
+        L.os_server_get_stats.restype = ctypes.c_int
+        L.os_server_get_stats.argtypes = [_vp, ctypes.POINTER(os_server_stats)]
+        L.os_server_replay.restype = ctypes.c_int
+        L.os_server_replay.argtypes = [_vp, ctypes.POINTER(os_request), ctypes.POINTER(ctypes.c_double), _u32,
+                                       ctypes.POINTER(os_result)]
+        L.os_server_destroy.restype = ctypes.c_int
+        L.os_server_destroy.argtypes = [_vp]
         L.os_read_counters.restype = ctypes.c_int
         L.os_read_counters.argtypes = [_vp, _vp, ctypes.POINTER(os_counters)]
         cls_p = ctypes.POINTER(os_seg_class)
@@ -269,3 +304,49 @@ def os_tune_segmented(key_type: int, d_keys_in: int, d_keys_out: int, d_vals_in:
                                  h_seg_offsets, nseg, seed & ((1 << 64) - 1), d_ws, ws_bytes, stream, reps, arr,
                                  max_classes, ctypes.byref(k), ctypes.byref(ms))
     return rc, [arr[i] for i in range(k.value)], float(ms.value)
+
+
+def os_server_create(d_arena: int, arena_bytes: int, streams: int, max_inflight: int) -> tuple[int, int]:
+    """Returns (status, server handle)."""
+    cfg = os_server_config(d_arena, arena_bytes, streams, max_inflight)
+    h = _vp(None)
+    rc = lib().os_server_create(ctypes.byref(cfg), ctypes.byref(h))
+    return rc, (h.value or 0)
+
+
+def os_server_submit(server: int, req: os_request) -> tuple[int, int]:
+    """Returns (status, ticket)."""
+    t = _u64(0)
+    rc = lib().os_server_submit(server, ctypes.byref(req), ctypes.byref(t))
+    return rc, int(t.value)
+
+
+def os_server_poll(server: int, max_results: int = 64, timeout_us: int = 0) -> tuple[int, list]:
+    arr = (os_result * max(1, max_results))()
+    k = _u32(0)
+    rc = lib().os_server_poll(server, arr, max_results, timeout_us, ctypes.byref(k))
+    return rc, [arr[i] for i in range(k.value)]
+
+
+def os_server_release(server: int, ticket: int) -> int:
+    return lib().os_server_release(server, ticket)
+
+
+def os_server_get_stats(server: int) -> tuple[int, os_server_stats]:
+    st = os_server_stats()
+    rc = lib().os_server_get_stats(server, ctypes.byref(st))
+    return rc, st
+
+
+def os_server_replay(server: int, reqs, arrival_s) -> tuple[int, list]:
+    """reqs: a sequence of os_request; arrival_s: non-decreasing seconds."""
+    n = len(reqs)
+    ra = (os_request * max(1, n))(*reqs)
+    ta = (ctypes.c_double * max(1, n))(*arrival_s)
+    res = (os_result * max(1, n))()
+    rc = lib().os_server_replay(server, ra, ta, n, res)
+    return rc, [res[i] for i in range(n)]
+
+
+def os_server_destroy(server: int) -> int:
+    return lib().os_server_destroy(server)

@@ -44,6 +44,11 @@ S_EDGE_KIND = 81
 S_EDGE_BITS = 82
 S_PAYLOAD = 91
 S_SEGLEN = 101
+S_ARRIVE = 111
+S_REQKIND = 112
+S_REQLEN = 113
+S_REQOFF = 114
+S_REQSEED = 115
 
 DISTRIBUTIONS = ("uniform", "gaussian", "zero", "bucket", "staggered", "ggroup", "dup")
 
@@ -257,3 +262,31 @@ def segment_offsets(lengths: torch.Tensor) -> torch.Tensor:
     off = torch.zeros(lengths.numel() + 1, dtype=torch.int64)
     off[1:] = torch.cumsum(lengths.to(torch.int64), 0)
     return off
+
+
+def serving_trace(count: int, rate: float = 2000.0, lo: int = 4096, hi: int = 1 << 26,
+                  seed: int = 5) -> dict:
+    """A trace of sort requests arriving as a Poisson process.
+
+    Request i arrives at the sum of i + 1 exponential gaps -ln(1 - u)/rate (u the
+    unit double of u(seed, S_ARRIVE, i)); the top two bits of u(seed, S_REQKIND, i)
+    pick its key type (bit 63: float64, else int32) and values (bit 62: random
+    duplicates, else uniform), each with probability 1/2; its length is
+    log-uniform in [lo, hi) as in segment_lengths; its keys are the slice at
+    offset floor(u * (hi - n + 1)) of a shared source array of hi keys of that
+    type and distribution (so every input can stay resident on the device);
+    its sample seed is u(seed, S_REQSEED, i).
+    Returns CPU tensors / lists: arrival_s, dtype, dist, n, offset, req_seed."""
+    g = torch.arange(count, dtype=torch.int64)
+    gap = -torch.log1p(-_unit(seed, S_ARRIVE, g)) / rate
+    arrival = torch.cumsum(gap, 0)
+    kind = u64(seed, S_REQKIND, g)
+    is_f64 = (kind < 0).tolist()                       # bit 63
+    is_dup = (_lsr(kind, 62) & 1).bool().tolist()      # bit 62
+    n = torch.floor(lo * torch.pow(torch.tensor(hi / lo, dtype=torch.float64),
+                                   _unit(seed, S_REQLEN, g))).to(torch.int64)
+    off = torch.floor(_unit(seed, S_REQOFF, g) * (hi - n + 1).to(torch.float64)).to(torch.int64)
+    rseed = u64(seed, S_REQSEED, g)
+    return {"arrival_s": arrival.tolist(), "dtype": ["f64" if f else "i32" for f in is_f64],
+            "dist": ["dup" if d else "uniform" for d in is_dup], "n": n.tolist(), "offset": off.tolist(),
+            "req_seed": [int(x) & MASK64 for x in rseed.tolist()], "lo": lo, "hi": hi}
