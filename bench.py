@@ -47,10 +47,14 @@ def parse():
     ap.add_argument("--ref-sample", type=int, default=1 << 20, help="keys per step of --impl reference")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="sort", choices=["sort", "batched"],
-                    help="sort: one array (the headline line, with a 'batched' summary); batched: the "
-                         "batched segmented workload as the line's own metric")
+    ap.add_argument("--workload", default="sort", choices=["sort", "batched", "serving"],
+                    help="sort: one array (the headline line, with 'batched' and 'serving' summaries); batched / "
+                         "serving: that workload as the line's own metric")
     ap.add_argument("--no-batched", action="store_true", help="leave the batched summary out of the sort line")
+    ap.add_argument("--no-serving", action="store_true", help="leave the serving summary out of the sort line")
+    ap.add_argument("--requests", type=int, default=20000, help="serving: requests of the replayed trace")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrival rate, requests/s")
+    ap.add_argument("--budget-gb", type=float, default=60.0, help="serving: HBM budget (the server's arena)")
     ap.add_argument("--segments", type=int, default=10000)
     ap.add_argument("--no-tune", action="store_true", help="batched: the default class table, not tuned")
     ap.add_argument("--plain-steps", type=int, default=2, help="batched: timed steps of the per-array loop")
@@ -412,6 +416,115 @@ def cpu_baseline_batched(a, max_keys=1 << 23):
             "sample": f"first {cnt} arrays ({m} keys) of the batched workload, one oracle run each ({t:.2f} s)"}
 
 
+# ---- serving workload -----------------------------------------------------------------
+
+SERVE = {"lo": 4096, "hi": 1 << 26, "seed": 5, "streams": 8, "max_inflight": 64, "p": 1024, "s": 16}
+
+
+def serving_workload_name(a, count):
+    return (f"{count} sort requests, Poisson arrivals at {a.rate:g}/s, int32 or float64 (1/2 each), uniform or "
+            f"32-value duplicates (1/2 each), lengths log-uniform in [4096, 2^26], inputs resident on the "
+            f"device, {a.budget_gb:g} GB HBM budget, SqRan p={SERVE['p']} s={SERVE['s']}")
+
+
+def _quantile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = (len(xs) - 1) * q
+    lo = int(k)
+    hi = min(lo + 1, len(xs) - 1)
+    return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
+
+
+def run_serving(a, rank, world, local, count, saturation=1000):
+    """Open-loop replay of the serving trace through the native server, then the
+    same server saturated (all of the first `saturation` requests at once) for the
+    largest sustainable rate."""
+    import torch
+
+    import paper_1608_08648_gb300 as oss
+    from paper_1608_08648_gb300 import inputs
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(local)
+    trace = inputs.serving_trace(count, a.rate, SERVE["lo"], SERVE["hi"], seed=SERVE["seed"] + rank)
+    src = {(dt, dist): inputs.keys(dist, SERVE["hi"], dt, seed=SERVE["seed"] + rank, device=dev)
+           for dt in ("i32", "f64") for dist in ("uniform", "dup")}
+    srv = oss.Server(int(a.budget_gb * 1e9), streams=SERVE["streams"], max_inflight=SERVE["max_inflight"], device=dev)
+
+    def req(i):
+        dt, dist, n, off = trace["dtype"][i], trace["dist"][i], trace["n"][i], trace["offset"][i]
+        return srv.request(src[(dt, dist)][off:off + n], "ran", SERVE["p"], SERVE["s"], trace["req_seed"][i], dt)
+
+    reqs = [req(i) for i in range(count)]
+    keys_total = sum(trace["n"])
+    # warm-up: 64 requests at once; one result checked against its solo sort
+    w = srv.replay(reqs[:64], [0.0] * min(64, count))
+    assert all(r.status == 0 for r in w)
+    t = srv.submit(src[(trace["dtype"][0], trace["dist"][0])][trace["offset"][0]:trace["offset"][0] + trace["n"][0]],
+                   "ran", SERVE["p"], SERVE["s"], trace["req_seed"][0], trace["dtype"][0])
+    res = []
+    while not res:
+        res = srv.poll(timeout_us=100_000)
+    ref, _, _ = oss.sort(src[(trace["dtype"][0], trace["dist"][0])][trace["offset"][0]:trace["offset"][0] +
+                                                                     trace["n"][0]],
+                         split="ran", p=SERVE["p"], s=SERVE["s"], seed=trace["req_seed"][0], key_type=trace["dtype"][0])
+    torch.cuda.synchronize()
+    assert torch.equal(res[0][2].view(torch.int64) if trace["dtype"][0] == "f64" else res[0][2],
+                       ref.view(torch.int64) if trace["dtype"][0] == "f64" else ref), "server result differs"
+    srv.release(t)
+
+    clocks = Clocks(local)
+    barrier(world)
+    clocks.start()
+    time.sleep(0.3)
+    l0 = oss.os_launch_count()
+    out = srv.replay(reqs, trace["arrival_s"])
+    launches = oss.os_launch_count() - l0
+    clk = clocks.stop()
+    assert all(r.status == 0 for r in out), "a request failed"
+    lat = [(r.done_s - r.submit_s) * 1e3 for r in out]
+    wait = [(r.admit_s - r.submit_s) * 1e3 for r in out]
+    span = max(r.done_s for r in out) - min(r.submit_s for r in out)
+    sustained = keys_total / span
+    st = srv.stats()
+
+    m = min(saturation, count)
+    sat = srv.replay(reqs[:m], [0.0] * m)
+    sat_span = max(r.done_s for r in sat) - min(r.submit_s for r in sat)
+    sat_keys = sum(trace["n"][:m])
+    srv.close()
+    del src
+    torch.cuda.empty_cache()
+    return {"requests": count, "keys": keys_total, "span_s": span, "value": world * sustained,
+            "offered": keys_total / trace["arrival_s"][-1],
+            "latency_ms": {"p50": _quantile(lat, 0.5), "p90": _quantile(lat, 0.9), "p99": _quantile(lat, 0.99),
+                           "max": max(lat), "mean": sum(lat) / len(lat)},
+            "queue_wait_ms": {"p50": _quantile(wait, 0.5), "p99": _quantile(wait, 0.99)},
+            "capacity": {"value": world * sat_keys / sat_span, "requests": m,
+                         "note": "the first requests of the trace submitted at once"},
+            "arena_peak_gb": st["arena_peak"] / 1e9, "max_inflight_seen": st["max_inflight_seen"],
+            "gpu_launches": launches, "clocks": clk}
+
+
+def run_serving_line(a, rank, world, local):
+    sv = run_serving(a, rank, world, local, a.requests)
+    res = {"metric": "keys/s (serving, sustained)", "value": sv["value"], "unit": "keys/s", "n_gpus": world,
+           "steps": 1, "warmup": 1, "ms_per_step": sv["span_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "i32+f64", "data": "synthetic",
+           "config": {"workload": serving_workload_name(a, a.requests), "requests": a.requests, "rate": a.rate,
+                      "budget_gb": a.budget_gb, "streams": SERVE["streams"], "max_inflight": SERVE["max_inflight"],
+                      "l2": "inputs larger than L2 (no flush needed)", "parallelism": "replicas"},
+           "latency_ms": sv["latency_ms"], "queue_wait_ms": sv["queue_wait_ms"], "offered": sv["offered"],
+           "capacity": sv["capacity"], "arena_peak_gb": sv["arena_peak_gb"],
+           "max_inflight_seen": sv["max_inflight_seen"], "roofline": None,
+           "e2e": None, "e2e_note": "requests arrive with their keys resident on the device (the workload's "
+                                    "definition); the host-copy variant is measured by the sort line's e2e",
+           "gpu_launches": sv["gpu_launches"], "clocks": sv["clocks"]}
+    return res
+
+
 # ---- our arm ------------------------------------------------------------------------
 
 def run_ours(a, rank, world, local):
@@ -562,6 +675,14 @@ def run_ours(a, rank, world, local):
                           "speedup_vs_plain": bt["speedup_vs_plain"], "classes": bt["classes"],
                           "tuned": bt["tuned"], "e2e": bt["e2e"], "roofline": bt["roofline"],
                           "gpu_launches": bt["gpu_launches"], "graph_kernels": bt["graph_kernels"]}
+    if not a.no_serving:
+        torch.cuda.empty_cache()
+        count = min(a.requests, 4000)
+        sv = run_serving(a, rank, world, local, count, saturation=500)
+        res["serving"] = {"workload": serving_workload_name(a, count), "value": sv["value"], "unit": "keys/s",
+                          "offered": sv["offered"], "latency_ms": sv["latency_ms"], "capacity": sv["capacity"],
+                          "arena_peak_gb": sv["arena_peak_gb"], "max_inflight_seen": sv["max_inflight_seen"],
+                          "gpu_launches": sv["gpu_launches"]}
     return res
 
 
@@ -622,6 +743,42 @@ def run_reference(a, rank, world):
     from paper_1608_08648_gb300 import inputs
     if rank != 0:
         return None
+    if a.workload == "serving":
+        import numpy as np
+        tr = inputs.serving_trace(a.requests, a.rate, SERVE["lo"], SERVE["hi"], seed=SERVE["seed"])
+        pick, m = [], 0        # requests in trace order that fit the sample's key budget
+        for i in range(a.requests):
+            if m + tr["n"][i] <= a.ref_sample:
+                pick.append(i)
+                m += tr["n"][i]
+        cnt = len(pick)
+        srcs = {}
+        for i in pick:
+            key = (tr["dtype"][i], tr["dist"][i])
+            if key not in srcs:
+                srcs[key] = inputs.keys(key[1], SERVE["hi"], key[0], seed=SERVE["seed"]).numpy()
+
+        def one_pass():
+            t0 = time.perf_counter()
+            for i in pick:
+                x = srcs[(tr["dtype"][i], tr["dist"][i])][tr["offset"][i]:tr["offset"][i] + tr["n"][i]]
+                oracle.sort(x, tr["dtype"][i], "ran", SERVE["p"], SERVE["s"], seed=tr["req_seed"][i])
+            return time.perf_counter() - t0
+
+        for _ in range(a.warmup):
+            one_pass()
+        ts = [one_pass() for _ in range(a.steps)]
+        t = statistics.median(ts)
+        v = m / t
+        return {"impl": "reference", "metric": "keys/s (serving, sustained)", "value": v, "unit": "keys/s",
+                "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32+f64",
+                "data": "synthetic",
+                "config": {"workload": serving_workload_name(a, a.requests), "parallelism": "replicas"},
+                "cpu_baseline": {"value": v, "unit": "keys/s", "kind": "oracle", "cores": 1,
+                                 "sample": f"{cnt} requests of the trace in arrival order that fit {a.ref_sample} "
+                                           f"keys ({m} keys), sorted one after another, no arrival gaps"},
+                "e2e": {"value": v, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     if a.workload == "batched":
         cb = None
         for _ in range(a.warmup):
@@ -668,7 +825,12 @@ def main():
     if a.impl == "reference":
         res = run_reference(a, rank, world)
     else:
-        res = run_batched_line(a, rank, world, local) if a.workload == "batched" else run_ours(a, rank, world, local)
+        if a.workload == "batched":
+            res = run_batched_line(a, rank, world, local)
+        elif a.workload == "serving":
+            res = run_serving_line(a, rank, world, local)
+        else:
+            res = run_ours(a, rank, world, local)
     if rank == 0 and res is not None:
         print(json.dumps(res), flush=True)
     if world > 1:
