@@ -16,6 +16,7 @@
 #include "../../include/ossort.h"
 #include "kernels.cuh"
 #include "profile.cuh"
+#include "segkernels.cuh"
 
 namespace ossort {
 
@@ -52,57 +53,199 @@ int occupancy(K kernel, int threads, size_t smem) {
     return occ > 0 ? occ : 1;
 }
 
-// Sort every segment of ss (stably, in the tagged order of positions inside
-// the segment).  Level-0 data is in src (read only); other and alt are scratch
-// buffers of the same length (alt may be src when src is writable); the sorted
-// segments land in out (which may be other).
+// ---------------------------------------------------------------------------
+// Segmented sort core (kernels of segkernels.cuh), shared by the bucket phase
+// of every sort and by the batched entry point.
+// ---------------------------------------------------------------------------
+
+// Upper bounds, from n, the number of segments and the class table alone, of
+// the planned totals (the workspace is sized by them).  A segment g that is
+// partitioned by a class has len_g >= 2 p_g s_g, so p_g <= len_g / (2 s_min);
+// with automatic p, p_g <= len_g / auto_child + 1.  A segment has at most
+// SEG_MAX_TILES tiles and at most len_g / tile_min + 1.
+struct SegBounds {
+    uint64_t tiles = 0, buckets = 0, hist = 0;
+    int maxp = 1;
+    bool any_part = false;
+};
+
+inline SegBounds seg_bounds_of(uint64_t n, uint32_t nseg, const SegClasses& cls) {
+    SegBounds b;
+    uint64_t smin = ~0ull, tmin = ~0ull;
+    for (uint32_t k = 0; k < cls.n; ++k) {
+        if (cls.c[k].p < 2 && !(cls.auto_child && k > 0)) continue;
+        b.any_part = true;
+        b.maxp = std::max<int>(b.maxp, (int)cls.c[k].p);
+        smin = std::min<uint64_t>(smin, cls.c[k].s);
+        tmin = std::min<uint64_t>(tmin, cls.c[k].tile);
+    }
+    uint64_t extra = 0;      // buckets beyond one per segment
+    if (b.any_part) extra += n / (2 * smin) + 1;
+    if (cls.auto_child) {
+        b.any_part = true;
+        b.maxp = std::max<int>(b.maxp, (int)cls.auto_pmax);
+        tmin = std::min<uint64_t>(tmin, cls.c[0].tile);
+        extra += n / cls.auto_child + 1;
+    }
+    if (!b.any_part) {
+        b.buckets = nseg;
+        return b;
+    }
+    b.tiles = std::min<uint64_t>(n / tmin + 1 + nseg, (uint64_t)SEG_MAX_TILES * nseg);
+    b.buckets = std::min<uint64_t>((uint64_t)nseg * b.maxp, nseg + extra);
+    b.hist = std::min<uint64_t>((uint64_t)b.maxp * (n / tmin + 1) + b.buckets, (uint64_t)SEG_MAX_TILES * b.buckets);
+    return b;
+}
+
+// Class table of the bucket phase: buckets up to a CTA's capacity are sorted
+// whole; a larger one is split by SqRan into children of about 0.72 of the
+// capacity (p from its length, s up to 64).
+template <class O>
+SegClasses bucket_classes() {
+    constexpr uint32_t CAP = (uint32_t)Cap<O>::v;
+    SegClasses t{};
+    t.n = 1;
+    t.c[0] = SegClass{CAP, 1u, 1u, 4096u, 0u};
+    t.auto_child = (CAP * 18u) / 25u;
+    t.auto_pmax = 1024;                 // s >= 4 with p s <= SEG_SAMPLE
+    t.auto_s = 64;
+    return t;
+}
+
+// Sort every segment of `src` into the same range of kout: segments above
+// their class's cutoff are partitioned by SqRan (k_seg_*), then every bucket
+// and every segment kept whole is sorted by the repartition levels (k_repart)
+// and the shared-memory sorts (k_leaf).  Buffers: 0 = kin (read only, unless it
+// is also alt), 1 = kout, 2 = alt (n keys of scratch; may be kin when every
+// segment longer than a leaf is partitioned, which bucket_classes guarantees).
 template <class KT, bool HV>
-void segment_sort(Ctx& c, SegSpec ss, const typename KT::T* src, const uint32_t* vsrc, typename KT::T* other,
-                  uint32_t* vother, typename KT::T* alt, uint32_t* valt, typename KT::T* out, uint32_t* vout,
-                  uint64_t seed) {
+void seg_core(Ctx& c, const SegSource& src, const SegClasses& cls, const typename KT::T* kin, const uint32_t* vin,
+              typename KT::T* kout, uint32_t* vout, typename KT::T* alt, uint32_t* valt, uint64_t seed,
+              const os_seg_stats* stats) {
+    using T = typename KT::T;
     using O = typename KT::O;
-    using L = BucketSmem<KT, HV>;
-    constexpr uint64_t CAP = (uint64_t)L::CAP;
-    if (ss.nseg == 0 || ss.n == 0) return;
+    using LE = LeafElem<O, true>;
+    using E = typename LE::E;
+    constexpr uint32_t CAP = (uint32_t)Cap<O>::v;
+    const uint64_t n = src.n;
+    const uint32_t nseg = src.nseg;
+    const SegBounds B = seg_bounds_of(n, nseg, cls);
+    SegRec* rec = c.ar.take<SegRec>(nseg);
+    uint32_t* tile0 = c.ar.take<uint32_t>((size_t)nseg + 1);
+    SegTotals* tot = c.ar.take<SegTotals>(1);
+    O* spl_o = c.ar.take<O>(B.buckets);
+    uint32_t* spl_t = c.ar.take<uint32_t>(B.buckets);
+    uint32_t* bsize = c.ar.take<uint32_t>(B.buckets);
+    uint32_t* hist = B.any_part ? c.ar.take<uint32_t>(B.hist) : nullptr;
+    uint16_t* bid = B.any_part ? c.ar.take<uint16_t>(n) : nullptr;
+    WorkLists wl{};
+    wl.counts = c.ar.take<uint32_t>(MAX_DEPTH + 1);
+    wl.part_cap = (uint32_t)(n / CAP + 1);
+    wl.leaf_cap = (uint32_t)(B.buckets + (uint64_t)MAX_DEPTH * 6 * wl.part_cap);
+    wl.leaf = c.ar.take<WorkItem>(wl.leaf_cap);
+    wl.part[0] = c.ar.take<WorkItem>(wl.part_cap);
+    wl.part[1] = c.ar.take<WorkItem>(wl.part_cap);
+    if (!c.live()) return;
+
+    const bool nest = c.nested;
+    os_memset_async(wl.counts, 0, sizeof(uint32_t) * (MAX_DEPTH + 1), c.st);
+    OS_LAUNCH(c.st, nest ? "k_seg_plan.sample" : "k_seg_plan",
+              k_seg_plan<<<1, 1024, 0, c.st>>>(src, cls, seed, rec, tile0, tot, B.tiles, B.buckets, B.hist,
+                                               c.status));
+    const uint32_t gseg = std::max<uint32_t>(1, std::min<uint32_t>(nseg, (uint32_t)c.num_sms * 8));
+    if (B.any_part) {
+        const size_t sm_spl = sizeof(E) * padded_len<E>(SEG_SAMPLE);
+        cudaFuncSetAttribute(k_seg_splitters<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_spl);
+        const uint32_t g_spl = std::min<uint32_t>(
+            nseg, (uint32_t)(c.num_sms * occupancy(k_seg_splitters<KT>, SEG_SPL_NT, sm_spl)));
+        OS_LAUNCH(c.st, nest ? "k_seg_splitters.sample" : "k_seg_splitters",
+                  k_seg_splitters<KT><<<std::max<uint32_t>(g_spl, 1), SEG_SPL_NT, sm_spl, c.st>>>(
+                      kin, rec, nseg, tot, spl_o, spl_t, c.status));
+        const size_t sm_c = seg_classify_smem<KT>(B.maxp);
+        cudaFuncSetAttribute(k_seg_classify<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c);
+        const uint32_t g_c = (uint32_t)(c.num_sms * occupancy(k_seg_classify<KT>, SEG_NT, sm_c));
+        OS_LAUNCH(c.st, nest ? "k_seg_classify.sample" : "k_seg_classify",
+                  k_seg_classify<KT><<<g_c, SEG_NT, sm_c, c.st>>>(kin, rec, tile0, nseg, tot, spl_o, spl_t, B.maxp,
+                                                                   hist, bid));
+    }
+    OS_LAUNCH(c.st, nest ? "k_seg_scan.sample" : "k_seg_scan",
+              k_seg_scan<<<gseg, SEG_SCAN_NT, 0, c.st>>>(rec, nseg, tot, hist, bsize, wl, CAP,
+                                                         (uint32_t)(static_cast<const void*>(alt) ==
+                                                                    static_cast<const void*>(kin)),
+                                                         c.status, c.status + 1,
+                                                         reinterpret_cast<unsigned long long*>(c.status + 4)));
+    if (B.any_part) {
+        const size_t sm_s = seg_scatter_smem<KT, HV>(B.maxp);
+        cudaFuncSetAttribute(k_seg_scatter<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_s);
+        const uint32_t g_s = (uint32_t)(c.num_sms * occupancy(k_seg_scatter<KT, HV>, SEG_NT, sm_s));
+        OS_LAUNCH(c.st, nest ? "k_seg_scatter.sample" : "k_seg_scatter",
+                  k_seg_scatter<KT, HV><<<g_s, SEG_NT, sm_s, c.st>>>(kin, vin, bid, rec, tile0, nseg, tot, hist,
+                                                                     B.maxp, kout, vout, c.status));
+    }
     SortBufs<KT> bufs;
-    bufs.k[0] = const_cast<typename KT::T*>(src);
-    bufs.v[0] = const_cast<uint32_t*>(vsrc);
-    bufs.k[1] = other;
-    bufs.v[1] = vother;
+    bufs.k[0] = const_cast<T*>(kin);
+    bufs.v[0] = const_cast<uint32_t*>(vin);
+    bufs.k[1] = kout;
+    bufs.v[1] = vout;
     bufs.k[2] = alt;
     bufs.v[2] = valt;
-    bufs.out = out;
+    bufs.out = kout;
     bufs.vout = vout;
-    WorkLists wl{};
-    const bool direct = ss.uniform && (ss.n + ss.nseg - 1) / ss.nseg <= CAP;
-    if (!direct) {
-        wl.counts = c.ar.take<uint32_t>(MAX_DEPTH + 1);
-        wl.part_cap = (uint32_t)(ss.n / CAP + 1);
-        wl.leaf_cap = (uint32_t)(ss.nseg + (uint64_t)MAX_DEPTH * 6 * wl.part_cap);
-        wl.leaf = c.ar.take<WorkItem>(wl.leaf_cap);
-        wl.part[0] = c.ar.take<WorkItem>(wl.part_cap);
-        wl.part[1] = c.ar.take<WorkItem>(wl.part_cap);
-    }
-    if (!c.live()) return;
+    const SegSpec ss{nullptr, 0u, 0u, n};
+    using L = BucketSmem<KT, HV>;
+    cudaFuncSetAttribute(k_repart<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+    const uint32_t grid_r = (uint32_t)(c.num_sms * occupancy(k_repart<KT, HV>, BK_NT, L::bytes));
+    const uint64_t inner_seed = sm_mix(seed ^ 0x5E6D5E6Dull);
+    for (int level = 1; level < MAX_DEPTH; ++level)
+        OS_LAUNCH(c.st, nest ? "k_repart.sample" : "k_repart",
+                  k_repart<KT, HV><<<grid_r, BK_NT, L::bytes, c.st>>>(level, ss, bufs, wl, inner_seed, c.status,
+                                                                      c.status + 1,
+                                                                      reinterpret_cast<unsigned long long*>(c.status + 4)));
     const size_t leaf_smem = LeafSmem<KT, HV>::bytes;
     cudaFuncSetAttribute(k_leaf<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf_smem);
     constexpr int LNT = LeafCfg<O, HV>::NT;
     const uint32_t grid_l = (uint32_t)(c.num_sms * occupancy(k_leaf<KT, HV>, LNT, leaf_smem));
-    if (direct) {
-        OS_LAUNCH(c.st, c.nested ? "k_leaf.sample" : "k_leaf",
-                  k_leaf<KT, HV><<<std::min(ss.nseg, grid_l), LNT, leaf_smem, c.st>>>(true, ss, bufs, wl, seed, c.status));
+    OS_LAUNCH(c.st, nest ? "k_leaf.sample" : "k_leaf",
+              k_leaf<KT, HV><<<grid_l, LNT, leaf_smem, c.st>>>(false, ss, bufs, wl, inner_seed, c.status));
+    if (stats) {
+        OS_LAUNCH(c.st, "k_seg_export",
+                  k_seg_export<KT><<<gseg, 256, 0, c.st>>>(rec, nseg, tot, spl_o, spl_t, bsize, stats->bucket_cap,
+                                                           stats->bucket_base, stats->bucket_sizes,
+                                                           static_cast<T*>(stats->splitter_keys),
+                                                           stats->splitter_tags));
+    }
+}
+
+// Sort every segment of ss (stably, in the tagged order of positions inside
+// the segment) from src into the same range of out.  alt: scratch of n keys
+// (may be src when src may be overwritten).  Segments of at most a CTA's
+// capacity given as an even split are sorted directly in shared memory.
+template <class KT, bool HV>
+void segment_sort(Ctx& c, SegSpec ss, const typename KT::T* src, const uint32_t* vsrc, typename KT::T* out,
+                  uint32_t* vout, typename KT::T* alt, uint32_t* valt, uint64_t seed) {
+    using O = typename KT::O;
+    using L = BucketSmem<KT, HV>;
+    constexpr uint64_t CAP = (uint64_t)L::CAP;
+    if (ss.nseg == 0 || ss.n == 0) return;
+    const bool direct = ss.uniform && (ss.n + ss.nseg - 1) / ss.nseg <= CAP;
+    if (!direct) {
+        const SegSource s{nullptr, ss.uniform ? nullptr : ss.off, ss.nseg, ss.n};
+        seg_core<KT, HV>(c, s, bucket_classes<O>(), src, vsrc, out, vout, alt, valt, seed, nullptr);
         return;
     }
-    os_memset_async(wl.counts, 0, sizeof(uint32_t) * (MAX_DEPTH + 1), c.st);
-    cudaFuncSetAttribute(k_repart<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
-    const uint32_t grid_r = (uint32_t)(c.num_sms * occupancy(k_repart<KT, HV>, BK_NT, L::bytes));
-    for (int level = 0; level < MAX_DEPTH; ++level) {
-        const uint32_t g = level == 0 ? std::min(ss.nseg, grid_r) : grid_r;
-        OS_LAUNCH(c.st, c.nested ? "k_repart.sample" : "k_repart",
-                  k_repart<KT, HV><<<g, BK_NT, L::bytes, c.st>>>(level, ss, bufs, wl, seed, c.status, c.status + 1,
-                                                                 reinterpret_cast<unsigned long long*>(c.status + 4)));
-    }
-    OS_LAUNCH(c.st, c.nested ? "k_leaf.sample" : "k_leaf", k_leaf<KT, HV><<<grid_l, LNT, leaf_smem, c.st>>>(false, ss, bufs, wl, seed, c.status));
+    if (!c.live()) return;
+    SortBufs<KT> bufs{};
+    bufs.k[0] = const_cast<typename KT::T*>(src);
+    bufs.v[0] = const_cast<uint32_t*>(vsrc);
+    bufs.out = out;
+    bufs.vout = vout;
+    const WorkLists wl{};
+    const size_t leaf_smem = LeafSmem<KT, HV>::bytes;
+    cudaFuncSetAttribute(k_leaf<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf_smem);
+    constexpr int LNT = LeafCfg<O, HV>::NT;
+    const uint32_t grid_l = (uint32_t)(c.num_sms * occupancy(k_leaf<KT, HV>, LNT, leaf_smem));
+    OS_LAUNCH(c.st, c.nested ? "k_leaf.sample" : "k_leaf",
+              k_leaf<KT, HV><<<std::min(ss.nseg, grid_l), LNT, leaf_smem, c.st>>>(true, ss, bufs, wl, seed, c.status));
 }
 
 // Bins of the top-level splitter table: the power of two >= 2p (at most 2^13).
@@ -224,8 +367,7 @@ void sort_array(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, typenam
     constexpr uint32_t CAP = (uint32_t)Cap<O>::v;
     if (n == 0) return;
     if (n <= CAP) {
-        segment_sort<KT, HV>(c, SegSpec::even(1, n), src, vsrc, nullptr, nullptr, nullptr, nullptr, out, vout,
-                             seed);
+        segment_sort<KT, HV>(c, SegSpec::even(1, n), src, vsrc, out, vout, nullptr, nullptr, seed);
         return;
     }
     const uint32_t p = std::min<uint32_t>(1024, std::max<uint32_t>(2, pow2_ceil(n / (2 * CAP))));
@@ -238,7 +380,7 @@ void sort_array(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, typenam
     uint32_t* vw = HV ? c.ar.take<uint32_t>(n) : nullptr;
     splitters_ran<KT>(c, src, n, p, s, seed, spl_o, spl_t);
     partition_top<KT, HV>(c, src, vsrc, n, spl_o, spl_t, p, w, vw, boff, bsize);
-    segment_sort<KT, HV>(c, SegSpec::offsets(boff, p, n), w, vw, out, vout, w, vw, out, vout, sm_mix(seed ^ 0x54ull));
+    segment_sort<KT, HV>(c, SegSpec::offsets(boff, p, n), w, vw, out, vout, w, vw, sm_mix(seed ^ 0x54ull));
 }
 
 // Device results of one user-level sort (for statistics).
@@ -277,15 +419,15 @@ void sort_top(Ctx& c, const typename KT::T* kin, typename KT::T* kout, const uin
     if (prm.split == OS_RAN) {
         splitters_ran<KT>(c, kin, n, p, s, prm.seed, spl_o, spl_t);
         partition_top<KT, HV>(c, kin, vin, n, spl_o, spl_t, p, w1, vw1, boff, bsize);
-        segment_sort<KT, HV>(c, SegSpec::offsets(boff, p, n), w1, vw1, kout, vout, w1, vw1, kout, vout, internal_seed);
+        segment_sort<KT, HV>(c, SegSpec::offsets(boff, p, n), w1, vw1, kout, vout, w1, vw1, internal_seed);
     } else {
         T* w2 = c.ar.take<T>(n);
         uint32_t* vw2 = HV ? c.ar.take<uint32_t>(n) : nullptr;
         // Step 1: the p sequences sorted into w1 (stable).
-        segment_sort<KT, HV>(c, SegSpec::even(p, n), kin, vin, w2, vw2, w1, vw1, w1, vw1, internal_seed);
+        segment_sort<KT, HV>(c, SegSpec::even(p, n), kin, vin, w1, vw1, w2, vw2, internal_seed);
         splitters_det<KT>(c, w1, n, p, s, internal_seed, spl_o, spl_t);
         partition_top<KT, HV>(c, w1, vw1, n, spl_o, spl_t, p, w2, vw2, boff, bsize);
-        segment_sort<KT, HV>(c, SegSpec::offsets(boff, p, n), w2, vw2, kout, vout, w2, vw2, kout, vout, internal_seed);
+        segment_sort<KT, HV>(c, SegSpec::offsets(boff, p, n), w2, vw2, kout, vout, w2, vw2, internal_seed);
     }
 }
 

@@ -1,8 +1,8 @@
 // Block-wide merge sort of up to NT*IT elements held in registers (the
 // shared-memory bucket sort of step 5).
 //
-//  1. Every thread sorts its IT consecutive elements in registers with a
-//     bitonic network (compile-time compare-exchanges).
+//  1. Every thread sorts its IT consecutive elements in registers with
+//     Batcher's odd-even merge network (compile-time compare-exchanges).
 //  2. log2(len / IT) rounds merge pairs of sorted runs through shared memory.
 //     In a round a thread owns IT consecutive outputs of its pair: a merge-path
 //     binary search finds how many of them come from the left run (ai) and the
@@ -35,6 +35,61 @@ __device__ __forceinline__ void cas_up(E& a, E& b) {   // a <- min, b <- max
 
 template <class E>
 __device__ __forceinline__ E emin(const E& a, const E& b) { return E::lt(b, a) ? b : a; }
+
+// Single-word elements order as plain unsigned integers: min / max.
+template <>
+__device__ __forceinline__ void cas_up<E32>(E32& a, E32& b) {
+    const uint32_t lo = min(a.k, b.k), hi = max(a.k, b.k);
+    a.k = lo;
+    b.k = hi;
+}
+template <>
+__device__ __forceinline__ void cas_up<E64>(E64& a, E64& b) {
+    const uint64_t lo = min(a.k, b.k), hi = max(a.k, b.k);
+    a.k = lo;
+    b.k = hi;
+}
+template <>
+__device__ __forceinline__ E32 emin<E32>(const E32& a, const E32& b) { return E32{min(a.k, b.k)}; }
+template <>
+__device__ __forceinline__ E64 emin<E64>(const E64& a, const E64& b) { return E64{min(a.k, b.k)}; }
+
+// Batcher's odd-even merge sort of x[0..IT) ascending (IT a power of two): 191
+// compare-exchanges for 32 elements against 240 for the bitonic network.  The
+// network is unrolled by template recursion so that every index is a
+// compile-time constant (the elements stay in registers).
+template <class E, int IT, int PP, int KK, int J, int I>
+__device__ __forceinline__ void oe_pairs(E (&x)[IT]) {
+    if constexpr (I < KK && I + J + KK < IT) {
+        if constexpr ((I + J) / (2 * PP) == (I + J + KK) / (2 * PP)) cas_up(x[I + J], x[I + J + KK]);
+        oe_pairs<E, IT, PP, KK, J, I + 1>(x);
+    }
+}
+template <class E, int IT, int PP, int KK, int J>
+__device__ __forceinline__ void oe_blocks(E (&x)[IT]) {
+    if constexpr (J + KK < IT) {
+        oe_pairs<E, IT, PP, KK, J, 0>(x);
+        oe_blocks<E, IT, PP, KK, J + 2 * KK>(x);
+    }
+}
+template <class E, int IT, int PP, int KK>
+__device__ __forceinline__ void oe_stages(E (&x)[IT]) {
+    if constexpr (KK >= 1) {
+        oe_blocks<E, IT, PP, KK, KK % PP>(x);
+        oe_stages<E, IT, PP, KK / 2>(x);
+    }
+}
+template <class E, int IT, int PP>
+__device__ __forceinline__ void oe_merges(E (&x)[IT]) {
+    if constexpr (PP < IT) {
+        oe_stages<E, IT, PP, PP>(x);
+        oe_merges<E, IT, 2 * PP>(x);
+    }
+}
+template <class E, int IT>
+__device__ __forceinline__ void oddeven_sort_regs(E (&x)[IT]) {
+    oe_merges<E, IT, 1>(x);
+}
 
 // Bitonic sort of x[0..IT) ascending (IT a power of two); every compare-exchange
 // and its direction are fixed at compile time.
@@ -71,7 +126,12 @@ template <class E, int NT, int IT>
 __device__ __forceinline__ void merge_sort_block(E (&x)[IT], E* sk, int len) {
     const int base = threadIdx.x * IT;
     const bool active = base < len;
-    if (active) bitonic_sort_regs<E, IT>(x);
+    if (active) {
+        // (key, position) triples keep the bitonic network: its shorter live
+        // ranges fit the 64-register budget of the 512-thread leaf.
+        if constexpr (sizeof(E) <= 8) oddeven_sort_regs<E, IT>(x);
+        else bitonic_sort_regs<E, IT>(x);
+    }
     for (int run = IT; run < len; run *= 2) {
         // A pair of runs that fits in one warp's elements is merged by that warp
         // alone, so only the larger rounds need the whole block.

@@ -1,541 +1,30 @@
-// Batched segmented sort: many independent arrays (segments of one buffer)
-// sorted by one fixed sequence of persistent kernels, each of which walks the
-// whole segment table.  Every segment g is sorted exactly as SqRan (Algorithm 2,
-// sample on original positions) sorts it alone with the parameters of its length
-// class and the seed u(seed, 2, g):
+// Batched segmented sort (os_sort_segmented): many independent arrays held
+// back to back in one buffer, every one sorted exactly as SqRan (Algorithm 2,
+// sample on original positions) sorts it alone with the parameters of its
+// length class and the seed u(seed, 2, g), by the fixed kernel sequence of
+// seg_core (driver.cuh):
 //
 //   k_seg_plan       per segment: class, p_g, s_g, tiles; exclusive scans of
 //                    tiles, buckets and histogram entries (one CTA)
-//   k_seg_splitters  step 2-3 per segment: p_g s_g - 1 random positions, the
+//   k_seg_splitters  steps 2-3 per segment: p_g s_g - 1 random positions, the
 //                    tagged sample sorted in shared memory, p_g - 1 splitters
 //   k_seg_classify   step 4: bucket of every key of every partitioned segment,
 //                    per-tile bucket counts
 //   k_seg_scan       per segment: bucket-major scan of its tile counts, bucket
 //                    sizes, and the work items of step 5
 //   k_seg_scatter    step 4: keys (and payloads) into contiguous buckets
-//   k_repart/k_leaf  step 5 (kernels.cuh): every bucket, and every segment too
-//                    small to sample, sorted through the shared work lists
+//   k_repart/k_leaf  step 5: every bucket, and every segment too small to
+//                    sample, sorted through the shared work lists
 //
-// A segment whose class has p = 1, or that is shorter than 2 p s (the small-n
-// rule of the plain sort), is one unit of step 5.  The host only knows n, the
-// number of segments and the class table, so the launch sequence does not
-// depend on the segment lengths: it can be captured once in a CUDA graph and
-// replayed for new keys and new offsets of the same totals.
+// The host only knows n, the number of segments and the class table, so the
+// launch sequence does not depend on the segment lengths: it can be captured
+// once in a CUDA graph and replayed for new keys and new offsets of the same
+// totals.
 #pragma once
 
 #include "driver.cuh"
 
 namespace ossort {
-
-constexpr int SEG_NT = 256;                 // threads of classify / scatter
-constexpr int SEG_WARPS = SEG_NT / 32;
-constexpr int SEG_IT = 8;                   // keys per thread per sub-tile
-constexpr int SEG_SUB = SEG_NT * SEG_IT;    // 2048 keys: tiles are multiples of this
-constexpr int SEG_SPL_NT = 512;             // threads of the per-segment sample sort
-constexpr int SEG_SPL_IT = 8;
-constexpr int SEG_SAMPLE = SEG_SPL_NT * SEG_SPL_IT;   // largest p s (the sample is p s - 1)
-constexpr int SEG_MAX_CLASSES = 32;
-constexpr int SEG_SCAN_NT = 256;
-constexpr int SEG_SCAN_CHUNK = 4096;
-constexpr uint32_t ERR_SEGS = 16u;          // segment offsets not non-decreasing from 0 to n
-
-struct SegClass {
-    uint64_t max_len;
-    uint32_t p, s, tile, pad;
-};
-struct SegClasses {
-    SegClass c[SEG_MAX_CLASSES];
-    uint32_t n;
-};
-
-// Per-segment plan written by k_seg_plan.
-struct SegRec {
-    uint32_t beg, len;
-    uint32_t p, s;       // p == 1: not partitioned (one unit of step 5)
-    uint32_t tile;       // keys per tile
-    uint32_t ntile;      // tiles (0 when p == 1)
-    uint32_t bkt0;       // first bucket of the segment in the bucket arrays
-    uint32_t hist0;      // first entry of its bucket-major tile-count matrix
-    uint64_t seed;       // seed of its sample
-};
-
-struct SegTotals {
-    uint32_t tiles, buckets, hist, ok;
-};
-
-__device__ __forceinline__ int seg_lbits(int p) {
-    int b = 1;
-    while ((1 << b) < 2 * p && b < 13) ++b;
-    return b;
-}
-
-// Segment owning global tile t: the last g with tile0[g] <= t (tile0 has nseg+1
-// non-decreasing entries, tile0[0] = 0 <= t < tile0[nseg]).
-__device__ __forceinline__ uint32_t seg_of_tile(const uint32_t* tile0, uint32_t nseg, uint32_t t) {
-    uint32_t lo = 0, hi = nseg;          // answer in [lo, hi)
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (tile0[mid] <= t) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
-
-// Inclusive warp scan of a 64-bit value.
-__device__ __forceinline__ uint64_t warp_incl_u64(uint64_t x) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    return x;
-}
-
-// ---------------------------------------------------------------------------
-// Plan: one CTA of 1024 threads walks the segments 1024 at a time.
-// ---------------------------------------------------------------------------
-static __global__ void __launch_bounds__(1024)
-k_seg_plan(const uint64_t* __restrict__ off, uint32_t nseg, uint64_t n, SegClasses cls, uint64_t seed,
-           SegRec* __restrict__ rec, uint32_t* __restrict__ tile0, SegTotals* __restrict__ tot, uint64_t tile_cap,
-           uint64_t bkt_cap, uint64_t hist_cap, uint32_t* status) {
-    __shared__ uint64_t wsum[3][32];
-    __shared__ uint64_t carry[3];
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    if (tid < 3) carry[tid] = 0;
-    const uint64_t state = sm_stream(seed, 2);
-    if (tid == 0 && nseg > 0 && (off[0] != 0 || off[nseg] != n)) atomicOr(status, ERR_SEGS);
-    __syncthreads();
-    for (uint32_t base = 0; base < nseg; base += 1024) {
-        const uint32_t g = base + tid;
-        uint64_t v[3] = {0, 0, 0};
-        SegRec r{};
-        if (g < nseg) {
-            uint64_t a = off[g], b = off[g + 1];
-            if (a > b || b > n) {
-                atomicOr(status, ERR_SEGS);
-                a = a > n ? n : a;
-                b = a;
-            }
-            r.beg = (uint32_t)a;
-            r.len = (uint32_t)(b - a);
-            uint32_t k = 0;
-            while (k + 1 < cls.n && (uint64_t)r.len > cls.c[k].max_len) ++k;
-            r.p = cls.c[k].p;
-            r.s = cls.c[k].s;
-            r.tile = cls.c[k].tile;
-            if (r.p > 1 && (uint64_t)r.len < 2ull * r.p * r.s) r.p = 1;   // too small to sample
-            r.ntile = r.p > 1 ? (r.len + r.tile - 1) / r.tile : 0;
-            r.seed = sm_at(state, g);
-            v[0] = r.ntile;
-            v[1] = r.p;
-            v[2] = (uint64_t)r.p * r.ntile;
-        }
-        uint64_t incl[3];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            incl[q] = warp_incl_u64(v[q]);
-            if (lane == 31) wsum[q][w] = incl[q];
-        }
-        __syncthreads();
-        if (w == 0) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const uint64_t x = warp_incl_u64(wsum[q][lane]);
-                wsum[q][lane] = x;
-            }
-        }
-        __syncthreads();
-        uint64_t ex[3];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) ex[q] = carry[q] + incl[q] - v[q] + (w > 0 ? wsum[q][w - 1] : 0);
-        if (g < nseg) {
-            r.bkt0 = (uint32_t)ex[1];
-            r.hist0 = (uint32_t)ex[2];
-            rec[g] = r;
-            tile0[g] = (uint32_t)ex[0];
-        }
-        __syncthreads();
-        if (tid < 3) carry[tid] += wsum[tid][31];
-        __syncthreads();
-    }
-    if (tid == 0) {
-        const bool ok = carry[0] <= tile_cap && carry[1] <= bkt_cap && carry[2] <= hist_cap;
-        if (!ok) atomicOr(status, ERR_SIZES);
-        tile0[nseg] = ok ? (uint32_t)carry[0] : 0u;
-        tot->tiles = ok ? (uint32_t)carry[0] : 0u;
-        tot->buckets = ok ? (uint32_t)carry[1] : 0u;
-        tot->hist = ok ? (uint32_t)carry[2] : 0u;
-        tot->ok = ok ? 1u : 0u;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Steps 2-3 per segment: positions floor(u_j len / 2^64) for j < p s - 1 from
-// stream 1 of the segment's seed, the tagged sample (key, position) sorted in
-// shared memory, splitter i at rank i s - 1.  One CTA per segment.
-// ---------------------------------------------------------------------------
-template <class KT>
-__global__ void __launch_bounds__(SEG_SPL_NT)
-k_seg_splitters(const typename KT::T* __restrict__ keys, const SegRec* __restrict__ rec, uint32_t nseg,
-                const SegTotals* __restrict__ tot, typename KT::O* __restrict__ spl_o,
-                uint32_t* __restrict__ spl_t, uint32_t* status) {
-    using O = typename KT::O;
-    using LE = LeafElem<O, true>;
-    using E = typename LE::E;
-    extern __shared__ __align__(16) char smem[];
-    E* ex = reinterpret_cast<E*>(smem);
-    if (!tot->ok) return;
-    for (uint32_t g = blockIdx.x; g < nseg; g += gridDim.x) {
-        const SegRec r = rec[g];
-        if (r.p < 2) continue;
-        const uint32_t m = r.p * r.s - 1;
-        if (m > (uint32_t)SEG_SAMPLE) {
-            if (threadIdx.x == 0) atomicOr(status, ERR_SAMPLE);
-            continue;
-        }
-        const uint64_t state = sm_stream(r.seed, 1);
-        E x[SEG_SPL_IT];
-        const int base = threadIdx.x * SEG_SPL_IT;
-#pragma unroll
-        for (int i = 0; i < SEG_SPL_IT; ++i) {
-            const uint32_t j = base + i;
-            if (j < m) {
-                const uint32_t pos = (uint32_t)__umul64hi(sm_at(state, j), (uint64_t)r.len);
-                x[i] = LE::make(KT::ord(keys[r.beg + pos]), pos);
-            } else {
-                x[i] = EMax<E>::v();
-            }
-        }
-        merge_sort_block<E, SEG_SPL_NT, SEG_SPL_IT>(x, ex, (int)m);
-#pragma unroll
-        for (int i = 0; i < SEG_SPL_IT; ++i) {
-            const uint32_t q = base + i + 1;          // rank + 1
-            if (q <= m && q % r.s == 0) {
-                const uint32_t k = q / r.s;           // splitter k (1 .. p-1)
-                spl_o[r.bkt0 + k - 1] = LE::key(x[i]);
-                spl_t[r.bkt0 + k - 1] = LE::pos(x[i]);
-            }
-        }
-    }
-}
-
-template <class KT>
-size_t seg_classify_smem(int maxp) {
-    int lb = 1;
-    while ((1 << lb) < 2 * maxp && lb < 13) ++lb;
-    return split_table_bytes<typename KT::O>(maxp, lb) + sizeof(uint32_t) * (maxp + 1);
-}
-
-// ---------------------------------------------------------------------------
-// Step 4, pass 1: every CTA owns a contiguous run of the global tiles; a tile
-// lies inside one segment.  The splitter table is rebuilt when the segment
-// changes.  Counts go to hist[hist0 + b * ntile + tile-in-segment].
-// ---------------------------------------------------------------------------
-template <class KT>
-__global__ void __launch_bounds__(SEG_NT, 3)
-k_seg_classify(const typename KT::T* __restrict__ keys, const SegRec* __restrict__ rec,
-               const uint32_t* __restrict__ tile0, uint32_t nseg, const SegTotals* __restrict__ tot,
-               const typename KT::O* __restrict__ spl_o, const uint32_t* __restrict__ spl_t, int maxp,
-               uint32_t* __restrict__ hist, uint16_t* __restrict__ bid) {
-    using O = typename KT::O;
-    extern __shared__ __align__(16) char smem[];
-    int maxlb = 1;
-    while ((1 << maxlb) < 2 * maxp && maxlb < 13) ++maxlb;
-    SplitTable<O> tb;
-    tb.bind(smem, maxp, maxlb);
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + split_table_bytes<O>(maxp, maxlb));   // [maxp + 1]
-    const uint32_t T = tot->tiles;
-    const uint32_t t0 = tile_lo(blockIdx.x, gridDim.x, T), t1 = tile_lo(blockIdx.x + 1, gridDim.x, T);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    SegRec r{};
-    uint32_t seg_t0 = 0, seg_t1 = 0;
-    for (uint32_t t = t0; t < t1; ++t) {
-        if (t >= seg_t1 || t < seg_t0) {
-            const uint32_t g = seg_of_tile(tile0, nseg, t);
-            r = rec[g];
-            seg_t0 = tile0[g];
-            seg_t1 = tile0[g + 1];
-            __syncthreads();                              // the previous table is no longer read
-            for (int i = threadIdx.x; i < (int)r.p - 1; i += SEG_NT)
-                tb.set(i, spl_o[r.bkt0 + i], spl_t[r.bkt0 + i]);
-            __syncthreads();
-            split_table_finish<O>(tb, (int)r.p - 1, seg_lbits((int)r.p));
-        }
-        const int p = (int)r.p;
-        const uint32_t tl = t - seg_t0;
-        for (int b = threadIdx.x; b <= p; b += SEG_NT) cnt[b] = 0;
-        __syncthreads();
-        for (uint32_t sub = 0; sub < r.tile; sub += SEG_SUB) {
-            const uint32_t lbase = tl * r.tile + sub;
-            if (lbase >= r.len) break;
-            const uint32_t base = lbase + w * (SEG_IT * 32) + lane;
-            O o[SEG_IT];
-#pragma unroll
-            for (int i = 0; i < SEG_IT; ++i) {
-                const uint32_t e = base + i * 32;
-                o[i] = e < r.len ? KT::ord(keys[r.beg + e]) : O(0);
-            }
-#pragma unroll
-            for (int i = 0; i < SEG_IT; ++i) {
-                const uint32_t e = base + i * 32;
-                int b = p;                                  // past the end: a spare counter
-                if (e < r.len) {
-                    b = split_find<O>(tb, o[i], e);
-                    bid[r.beg + e] = (uint16_t)b;
-                }
-                warp_count((uint32_t)b, cnt);
-            }
-        }
-        __syncthreads();
-        for (int b = threadIdx.x; b < p; b += SEG_NT) hist[r.hist0 + (size_t)b * r.ntile + tl] = cnt[b];
-        __syncthreads();
-    }
-}
-
-__device__ __forceinline__ void seg_push(const WorkLists& wl, uint32_t beg, uint32_t len, uint32_t buf, uint32_t cap,
-                                         uint32_t* status) {
-    if (len <= cap) push_item(wl.leaf, &wl.counts[0], wl.leaf_cap, beg, len, buf, status);
-    else push_item(wl.part[0], &wl.counts[1], wl.part_cap, beg, len, buf, status);
-}
-
-// ---------------------------------------------------------------------------
-// Per segment: exclusive bucket-major scan of its tile counts (in place: entry
-// (b, t) becomes the offset of tile t's keys of bucket b inside the segment),
-// bucket sizes, and the step-5 work items: every non-empty bucket (in buffer
-// 1, where the scatter puts it), or the whole segment (buffer 0, the input)
-// when it is not partitioned.  cap: the leaf capacity.
-// ---------------------------------------------------------------------------
-static __global__ void __launch_bounds__(SEG_SCAN_NT)
-k_seg_scan(const SegRec* __restrict__ rec, uint32_t nseg, const SegTotals* __restrict__ tot, uint32_t* hist,
-           uint32_t* __restrict__ bsize, WorkLists wl, uint32_t cap, uint32_t* status) {
-    __shared__ uint32_t buf[SEG_SCAN_CHUNK];
-    __shared__ uint32_t scratch[32];
-    if (!tot->ok) return;
-    for (uint32_t g = blockIdx.x; g < nseg; g += gridDim.x) {
-        const SegRec r = rec[g];
-        if (r.p < 2) {
-            if (threadIdx.x == 0) {
-                bsize[r.bkt0] = r.len;
-                if (r.len > 0) seg_push(wl, r.beg, r.len, 0u, cap, status);
-            }
-            continue;
-        }
-        const uint32_t M = r.p * r.ntile;
-        uint32_t* h = hist + r.hist0;
-        uint32_t carry = 0;
-        for (uint32_t c0 = 0; c0 < M; c0 += SEG_SCAN_CHUNK) {
-            const int len = (int)min((uint32_t)SEG_SCAN_CHUNK, M - c0);
-            for (int i = threadIdx.x; i < len; i += SEG_SCAN_NT) buf[i] = h[c0 + i];
-            const uint32_t t = block_exclusive_scan(buf, len, scratch);
-            for (int i = threadIdx.x; i < len; i += SEG_SCAN_NT) h[c0 + i] = buf[i] + carry;
-            carry += t;
-            __syncthreads();
-        }
-        if (carry != r.len) {
-            if (threadIdx.x == 0) atomicOr(status, ERR_SIZES);
-            continue;
-        }
-        for (uint32_t b = threadIdx.x; b < r.p; b += SEG_SCAN_NT) {
-            const uint32_t a = h[(size_t)b * r.ntile];
-            const uint32_t z = b + 1 < r.p ? h[(size_t)(b + 1) * r.ntile] : r.len;
-            bsize[r.bkt0 + b] = z - a;
-            if (z > a) seg_push(wl, r.beg + a, z - a, 1u, cap, status);
-        }
-        __syncthreads();
-    }
-}
-
-template <class KT, bool HV>
-size_t seg_scatter_smem(int maxp) {
-    using T = typename KT::T;
-    size_t b = sizeof(T) * SEG_SUB + (HV ? sizeof(uint32_t) * SEG_SUB : 0);
-    b += sizeof(uint32_t) * (maxp + 1) + sizeof(uint32_t) * maxp + sizeof(uint32_t) * 32;
-    b += sizeof(uint16_t) * SEG_SUB + (HV ? sizeof(uint16_t) * SEG_WARPS * (maxp + 1) : 0);
-    return b;
-}
-
-// ---------------------------------------------------------------------------
-// Step 4, pass 2: the tiles again; each tile starts its buckets' cursors at the
-// scanned offsets and moves its keys sub-tile by sub-tile, ranked as in
-// k_scatter (stable with a payload).  Output buffer: out.
-// ---------------------------------------------------------------------------
-template <class KT, bool HV>
-__global__ void __launch_bounds__(SEG_NT, 3)
-k_seg_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ vals,
-              const uint16_t* __restrict__ bid, const SegRec* __restrict__ rec, const uint32_t* __restrict__ tile0,
-              uint32_t nseg, const SegTotals* __restrict__ tot, const uint32_t* __restrict__ col, int maxp,
-              typename KT::T* __restrict__ out, uint32_t* __restrict__ vout, uint32_t* status) {
-    using T = typename KT::T;
-    extern __shared__ __align__(16) char smem[];
-    char* q = smem;
-    T* sk = reinterpret_cast<T*>(q);                     q += sizeof(T) * SEG_SUB;
-    uint32_t* sv = reinterpret_cast<uint32_t*>(q);       q += HV ? sizeof(uint32_t) * SEG_SUB : 0;
-    uint32_t* tile_off = reinterpret_cast<uint32_t*>(q); q += sizeof(uint32_t) * (maxp + 1);
-    uint32_t* cursor = reinterpret_cast<uint32_t*>(q);   q += sizeof(uint32_t) * maxp;
-    uint32_t* scratch = reinterpret_cast<uint32_t*>(q);  q += sizeof(uint32_t) * 32;
-    uint16_t* sb = reinterpret_cast<uint16_t*>(q);       q += sizeof(uint16_t) * SEG_SUB;
-    uint16_t* cnt = reinterpret_cast<uint16_t*>(q);      // HV: [SEG_WARPS][p + 1]
-
-    const uint32_t T_ = tot->tiles;
-    const uint32_t t0 = tile_lo(blockIdx.x, gridDim.x, T_), t1 = tile_lo(blockIdx.x + 1, gridDim.x, T_);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    SegRec r{};
-    uint32_t seg_t0 = 0, seg_t1 = 0;
-    for (uint32_t t = t0; t < t1; ++t) {
-        if (t >= seg_t1 || t < seg_t0) {
-            const uint32_t g = seg_of_tile(tile0, nseg, t);
-            r = rec[g];
-            seg_t0 = tile0[g];
-            seg_t1 = tile0[g + 1];
-        }
-        const int p = (int)r.p;
-        const int cstride = p + 1;
-        uint16_t* mycnt = cnt + w * cstride;
-        const uint32_t tl = t - seg_t0;
-        const uint32_t seg_end = r.beg + r.len;
-        __syncthreads();                                  // previous tile's cursors are no longer read
-        for (int b = threadIdx.x; b < p; b += SEG_NT) cursor[b] = r.beg + col[r.hist0 + (size_t)b * r.ntile + tl];
-        for (uint32_t sub = 0; sub < r.tile; sub += SEG_SUB) {
-            const uint32_t lbase = tl * r.tile + sub;
-            if (lbase >= r.len) break;
-            const uint32_t base = lbase + w * (SEG_IT * 32) + lane;
-            T kv[SEG_IT];
-            uint32_t br[SEG_IT];   // bucket << 16 | rank inside the sub-tile's part of the bucket
-#pragma unroll
-            for (int i = 0; i < SEG_IT; ++i) {
-                const uint32_t e = base + i * 32;
-                kv[i] = e < r.len ? keys[r.beg + e] : T(0);
-                br[i] = e < r.len ? (uint32_t)bid[r.beg + e] : (uint32_t)p;
-            }
-            if (HV) {
-                for (int b = lane; b <= p; b += 32) mycnt[b] = 0;
-            } else {
-                for (int b = threadIdx.x; b <= p; b += SEG_NT) tile_off[b] = 0;
-            }
-            __syncthreads();
-            if (HV) {
-                const int nbits = 32 - __clz(p);
-#pragma unroll
-                for (int i = 0; i < SEG_IT; ++i) {
-                    const int b = (int)br[i];
-                    const unsigned m = warp_peers((uint32_t)b, nbits);
-                    const uint32_t c0 = mycnt[b];
-                    br[i] = ((uint32_t)b << 16) | (c0 + __popc(m & lanemask_lt()));
-                    __syncwarp();
-                    if (lane == __ffs(m) - 1) mycnt[b] = (uint16_t)(c0 + __popc(m));
-                    __syncwarp();
-                }
-                __syncthreads();
-                for (int b = threadIdx.x; b < p; b += SEG_NT) {
-                    uint32_t run = 0;
-#pragma unroll
-                    for (int ww = 0; ww < SEG_WARPS; ++ww) {
-                        const uint32_t c = cnt[ww * cstride + b];
-                        cnt[ww * cstride + b] = (uint16_t)run;
-                        run += c;
-                    }
-                    tile_off[b] = run;
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < SEG_IT; ++i) {
-                    const uint32_t b = br[i];
-                    br[i] = (b << 16) | warp_slot(b, tile_off);
-                }
-            }
-            const uint32_t tvalid = block_exclusive_scan(tile_off, p, scratch);
-            if (threadIdx.x == 0) tile_off[p] = tvalid;
-#pragma unroll
-            for (int i = 0; i < SEG_IT; ++i) {
-                const int b = (int)(br[i] >> 16);
-                if (b < p) {
-                    const uint32_t loc = tile_off[b] + (HV ? mycnt[b] : 0u) + (br[i] & 0xFFFFu);
-                    if (loc >= (uint32_t)SEG_SUB) {
-                        flag_bounds(status, 10, loc);
-                        continue;
-                    }
-                    sk[loc] = kv[i];
-                    if (HV) sv[loc] = vals[r.beg + base + i * 32];
-                    sb[loc] = (uint16_t)b;
-                }
-            }
-            __syncthreads();
-            for (uint32_t j = threadIdx.x; j < tvalid; j += SEG_NT) {
-                const int b = sb[j];
-                const uint32_t dst = cursor[b] + (j - tile_off[b]);
-                if (dst < r.beg || dst >= seg_end) {
-                    flag_bounds(status, 11, dst);
-                    continue;
-                }
-                out[dst] = sk[j];
-                if (HV) vout[dst] = sv[j];
-            }
-            __syncthreads();
-            for (int b = threadIdx.x; b < p; b += SEG_NT) cursor[b] += tile_off[b + 1] - tile_off[b];
-            __syncthreads();
-        }
-    }
-}
-
-// Statistics: first bucket of every segment, and the splitters as keys.
-template <class KT>
-__global__ void k_seg_export(const SegRec* __restrict__ rec, uint32_t nseg, const SegTotals* __restrict__ tot,
-                             const typename KT::O* __restrict__ spl_o, const uint32_t* __restrict__ spl_t,
-                             const uint32_t* __restrict__ bsize, uint64_t cap, uint32_t* bucket_base,
-                             uint32_t* bucket_sizes, typename KT::T* spl_keys, uint32_t* spl_tags) {
-    const uint32_t nb = tot->buckets;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (bucket_base) {
-        for (uint64_t g = i0; g <= nseg; g += stride) bucket_base[g] = g < nseg ? rec[g].bkt0 : nb;
-    }
-    for (uint64_t b = i0; b < nb && b < cap; b += stride) {
-        if (bucket_sizes) bucket_sizes[b] = bsize[b];
-    }
-    // splitters: segment g's p - 1 splitters sit at [bkt0, bkt0 + p - 1)
-    for (uint64_t g = i0; g < nseg; g += stride) {
-        const SegRec r = rec[g];
-        for (uint32_t k = 0; k + 1 < r.p && r.bkt0 + k < cap; ++k) {
-            if (spl_keys) spl_keys[r.bkt0 + k] = KT::key(spl_o[r.bkt0 + k]);
-            if (spl_tags) spl_tags[r.bkt0 + k] = spl_t[r.bkt0 + k];
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Host side.
-// ---------------------------------------------------------------------------
-
-// Upper bounds, from n, the number of segments and the class table alone, of
-// the planned totals (the workspace is sized by them).  A segment g that is
-// partitioned has len_g >= 2 p_g s_g, so p_g <= len_g / (2 s_min); its tiles
-// number at most len_g / tile_min + 1.
-struct SegBounds {
-    uint64_t tiles = 0, buckets = 0, hist = 0;
-    int maxp = 1;
-    bool any_part = false;
-};
-
-inline SegBounds seg_bounds_of(uint64_t n, uint32_t nseg, const SegClasses& cls) {
-    SegBounds b;
-    uint64_t smin = ~0ull, tmin = ~0ull;
-    for (uint32_t k = 0; k < cls.n; ++k) {
-        if (cls.c[k].p < 2) continue;
-        b.any_part = true;
-        b.maxp = std::max<int>(b.maxp, (int)cls.c[k].p);
-        smin = std::min<uint64_t>(smin, cls.c[k].s);
-        tmin = std::min<uint64_t>(tmin, cls.c[k].tile);
-    }
-    if (!b.any_part) {
-        b.buckets = nseg;
-        return b;
-    }
-    b.tiles = n / tmin + 1 + nseg;
-    b.buckets = std::min<uint64_t>((uint64_t)nseg * b.maxp, nseg + n / (2 * smin) + 1);
-    b.hist = (uint64_t)b.maxp * (n / tmin + 1) + b.buckets;
-    return b;
-}
 
 // Everything one os_sort_segmented call needs, independent of the key type.
 struct SegArgs {
@@ -559,103 +48,9 @@ struct SegArgs {
     uint32_t* status;
 };
 
-template <class KT, bool HV>
-void seg_run(Ctx& c, SegArgs& a) {
-    using T = typename KT::T;
-    using O = typename KT::O;
-    using LE = LeafElem<O, true>;
-    using E = typename LE::E;
-    constexpr uint32_t CAP = (uint32_t)Cap<O>::v;
-    const SegBounds B = seg_bounds_of(a.n, a.nseg, a.cls);
-    SegRec* rec = c.ar.take<SegRec>(a.nseg);
-    uint32_t* tile0 = c.ar.take<uint32_t>((size_t)a.nseg + 1);
-    SegTotals* tot = c.ar.take<SegTotals>(1);
-    O* spl_o = c.ar.take<O>(B.buckets);
-    uint32_t* spl_t = c.ar.take<uint32_t>(B.buckets);
-    uint32_t* bsize = c.ar.take<uint32_t>(B.buckets);
-    uint32_t* hist = B.any_part ? c.ar.take<uint32_t>(B.hist) : nullptr;
-    uint16_t* bid = B.any_part ? c.ar.take<uint16_t>(a.n) : nullptr;
-    T* w = c.ar.take<T>(a.n);
-    uint32_t* vw = HV ? c.ar.take<uint32_t>(a.n) : nullptr;
-    WorkLists wl{};
-    wl.counts = c.ar.take<uint32_t>(MAX_DEPTH + 1);
-    wl.part_cap = (uint32_t)(a.n / CAP + 1);
-    wl.leaf_cap = (uint32_t)(B.buckets + (uint64_t)MAX_DEPTH * 6 * wl.part_cap);
-    wl.leaf = c.ar.take<WorkItem>(wl.leaf_cap);
-    wl.part[0] = c.ar.take<WorkItem>(wl.part_cap);
-    wl.part[1] = c.ar.take<WorkItem>(wl.part_cap);
-    if (!c.live()) return;
-
-    const T* kin = static_cast<const T*>(a.kin);
-    T* kout = static_cast<T*>(a.kout);
-    os_memset_async(wl.counts, 0, sizeof(uint32_t) * (MAX_DEPTH + 1), c.st);
-    OS_LAUNCH(c.st, "k_seg_plan",
-              k_seg_plan<<<1, 1024, 0, c.st>>>(a.off, a.nseg, a.n, a.cls, a.seed, rec, tile0, tot, B.tiles,
-                                               B.buckets, B.hist, c.status));
-    const uint32_t gseg = std::max<uint32_t>(1, std::min<uint32_t>(a.nseg, (uint32_t)c.num_sms * 8));
-    if (B.any_part) {
-        const size_t sm_spl = sizeof(E) * padded_len<E>(SEG_SAMPLE);
-        cudaFuncSetAttribute(k_seg_splitters<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_spl);
-        const uint32_t g_spl = std::min<uint32_t>(
-            a.nseg, (uint32_t)(c.num_sms * occupancy(k_seg_splitters<KT>, SEG_SPL_NT, sm_spl)));
-        OS_LAUNCH(c.st, "k_seg_splitters",
-                  k_seg_splitters<KT><<<std::max<uint32_t>(g_spl, 1), SEG_SPL_NT, sm_spl, c.st>>>(
-                      kin, rec, a.nseg, tot, spl_o, spl_t, c.status));
-        const size_t sm_c = seg_classify_smem<KT>(B.maxp);
-        cudaFuncSetAttribute(k_seg_classify<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c);
-        const uint32_t g_c = (uint32_t)(c.num_sms * occupancy(k_seg_classify<KT>, SEG_NT, sm_c));
-        OS_LAUNCH(c.st, "k_seg_classify",
-                  k_seg_classify<KT><<<g_c, SEG_NT, sm_c, c.st>>>(kin, rec, tile0, a.nseg, tot, spl_o, spl_t,
-                                                                   B.maxp, hist, bid));
-    }
-    OS_LAUNCH(c.st, "k_seg_scan",
-              k_seg_scan<<<gseg, SEG_SCAN_NT, 0, c.st>>>(rec, a.nseg, tot, hist, bsize, wl, CAP, c.status));
-    if (B.any_part) {
-        const size_t sm_s = seg_scatter_smem<KT, HV>(B.maxp);
-        cudaFuncSetAttribute(k_seg_scatter<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_s);
-        const uint32_t g_s = (uint32_t)(c.num_sms * occupancy(k_seg_scatter<KT, HV>, SEG_NT, sm_s));
-        OS_LAUNCH(c.st, "k_seg_scatter",
-                  k_seg_scatter<KT, HV><<<g_s, SEG_NT, sm_s, c.st>>>(kin, a.vin, bid, rec, tile0, a.nseg, tot,
-                                                                     hist, B.maxp, kout, a.vout, c.status));
-    }
-    // Step 5: the work lists hold every bucket (buffer 1 = kout) and every
-    // unpartitioned segment (buffer 0 = the input); the repartition levels
-    // below them alternate between w (buffer 2) and kout.
-    SortBufs<KT> bufs;
-    bufs.k[0] = const_cast<T*>(kin);
-    bufs.v[0] = const_cast<uint32_t*>(a.vin);
-    bufs.k[1] = kout;
-    bufs.v[1] = a.vout;
-    bufs.k[2] = w;
-    bufs.v[2] = vw;
-    bufs.out = kout;
-    bufs.vout = a.vout;
-    const SegSpec ss{nullptr, 0u, 0u, a.n};
-    using L = BucketSmem<KT, HV>;
-    cudaFuncSetAttribute(k_repart<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
-    const uint32_t grid_r = (uint32_t)(c.num_sms * occupancy(k_repart<KT, HV>, BK_NT, L::bytes));
-    const uint64_t inner_seed = sm_mix(a.seed ^ 0x5E6D5E6Dull);
-    for (int level = 1; level < MAX_DEPTH; ++level)
-        OS_LAUNCH(c.st, "k_repart",
-                  k_repart<KT, HV><<<grid_r, BK_NT, L::bytes, c.st>>>(level, ss, bufs, wl, inner_seed, c.status,
-                                                                      c.status + 1,
-                                                                      reinterpret_cast<unsigned long long*>(c.status + 4)));
-    const size_t leaf_smem = LeafSmem<KT, HV>::bytes;
-    cudaFuncSetAttribute(k_leaf<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf_smem);
-    constexpr int LNT = LeafCfg<O, HV>::NT;
-    const uint32_t grid_l = (uint32_t)(c.num_sms * occupancy(k_leaf<KT, HV>, LNT, leaf_smem));
-    OS_LAUNCH(c.st, "k_leaf", k_leaf<KT, HV><<<grid_l, LNT, leaf_smem, c.st>>>(false, ss, bufs, wl, inner_seed, c.status));
-    if (a.stats) {
-        const os_seg_stats& so = *a.stats;
-        OS_LAUNCH(c.st, "k_seg_export",
-                  k_seg_export<KT><<<gseg, 256, 0, c.st>>>(rec, a.nseg, tot, spl_o, spl_t, bsize, so.bucket_cap,
-                                                           so.bucket_base, so.bucket_sizes,
-                                                           static_cast<T*>(so.splitter_keys), so.splitter_tags));
-    }
-}
-
 template <class KT>
 int run_segmented(SegArgs& a) {
+    using T = typename KT::T;
     Ctx c;
     c.st = a.st;
     c.num_sms = a.num_sms;
@@ -663,8 +58,13 @@ int run_segmented(SegArgs& a) {
     c.ar.cap = a.ws_bytes;
     c.status = c.ar.take<uint32_t>(8);
     if (c.live()) os_memset_async(c.status, 0, 8 * sizeof(uint32_t), c.st);
-    if (a.has_vals) seg_run<KT, true>(c, a);
-    else seg_run<KT, false>(c, a);
+    T* alt = c.ar.take<T>(a.n);
+    uint32_t* valt = a.has_vals ? c.ar.take<uint32_t>(a.n) : nullptr;
+    const SegSource src{a.off, nullptr, a.nseg, a.n};
+    const T* kin = static_cast<const T*>(a.kin);
+    T* kout = static_cast<T*>(a.kout);
+    if (a.has_vals) seg_core<KT, true>(c, src, a.cls, kin, a.vin, kout, a.vout, alt, valt, a.seed, a.stats);
+    else seg_core<KT, false>(c, src, a.cls, kin, nullptr, kout, nullptr, alt, nullptr, a.seed, a.stats);
     a.used = c.ar.used;
     a.status = c.status;
     return c.ar.failed ? OS_ERR_WS : OS_OK;
