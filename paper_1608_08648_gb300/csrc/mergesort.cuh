@@ -5,12 +5,11 @@
 //     Batcher's odd-even merge network (compile-time compare-exchanges).
 //  2. log2(len / IT) rounds merge pairs of sorted runs through shared memory.
 //     In a round a thread owns IT consecutive outputs of its pair: a merge-path
-//     binary search finds how many of them come from the left run (ai) and the
-//     right run (bi).  Its outputs are then the IT smallest of A[ai, ai+IT) and
-//     B[bi, bi+IT); taking min(A[ai+i], B[bi+IT-1-i]) element by element yields
-//     exactly those IT elements as a bitonic sequence (the half-cleaner of a
-//     bitonic merge), which log2(IT) register stages sort.  Every step is data
-//     independent, so a thread's loads and compare-exchanges overlap.
+//     binary search finds where they start in the left run (ai) and the right
+//     run (bi); the thread then merges serially, keeping the two run heads in
+//     registers and refilling the consumed side with one shared load per output
+//     ((key, position) triples instead take the IT candidates of each run and
+//     sort their elementwise minimum, a bitonic sequence, in registers).
 //
 // Runs are padded: every thread stores all IT of its elements, and positions at
 // or beyond len hold +infinity, so a ragged last run needs no special case.  The
@@ -154,15 +153,42 @@ __device__ __forceinline__ void merge_sort_block(E (&x)[IT], E* sk, int len) {
                 if (E::lt(bv, av)) hi = mid;
                 else lo = mid + 1;
             }
-            const int ai = lo, bi = d - lo;
+            if constexpr (sizeof(E) <= 8) {
+                // Serial merge of the thread's IT outputs: the heads of both runs in
+                // registers, one shared load per output to refill the consumed side
+                // (ties go to the left run).
+                int ia = lo, ib = d - lo;
+                E av = ia < run ? A[pad_idx<E>(pb + ia)] : EMax<E>::v();
+                E bv = ib < run ? A[pad_idx<E>(pb + run + ib)] : EMax<E>::v();
 #pragma unroll
-            for (int i = 0; i < IT; ++i) {
-                const int ia = ai + i, ib = bi + IT - 1 - i;
-                const E av = ia < run ? A[pad_idx<E>(pb + ia)] : EMax<E>::v();
-                const E bv = ib < run ? A[pad_idx<E>(pb + run + ib)] : EMax<E>::v();
-                x[i] = emin(av, bv);
+                for (int i = 0; i < IT; ++i) {
+                    const bool take_b = E::lt(bv, av);
+                    x[i] = take_b ? bv : av;
+                    if (i + 1 < IT) {
+                        const int nx = take_b ? ib + 1 : ia + 1;
+                        const int nidx = take_b ? pb + run + nx : pb + nx;
+                        const E nv = nx < run ? A[pad_idx<E>(nidx)] : EMax<E>::v();
+                        ia += take_b ? 0 : 1;
+                        ib += take_b ? 1 : 0;
+                        av = take_b ? av : nv;
+                        bv = take_b ? nv : bv;
+                    }
+                }
+            } else {
+                // (key, position) triples: the IT smallest of A[ai, ai+IT) and
+                // B[bi, bi+IT) as min(A[ai+i], B[bi+IT-1-i]) (a bitonic sequence,
+                // the half-cleaner of a bitonic merge), sorted by log2(IT) register
+                // stages; fewer live registers than the serial merge of triples.
+                const int ai = lo, bi = d - lo;
+#pragma unroll
+                for (int i = 0; i < IT; ++i) {
+                    const int ia = ai + i, ib = bi + IT - 1 - i;
+                    const E av = ia < run ? A[pad_idx<E>(pb + ia)] : EMax<E>::v();
+                    const E bv = ib < run ? A[pad_idx<E>(pb + run + ib)] : EMax<E>::v();
+                    x[i] = emin(av, bv);
+                }
+                bitonic_merge_regs<E, IT>(x);
             }
-            bitonic_merge_regs<E, IT>(x);
         }
     }
     __syncthreads();
