@@ -214,7 +214,7 @@ static __global__ void k_bucket_offsets(const uint32_t* __restrict__ bsize, uint
 // shared-memory atomics, one per run of equal neighbours, hand out the slots.
 // ---------------------------------------------------------------------------
 template <class KT, bool HV>
-__global__ void __launch_bounds__(TOP_NT, 3)
+__global__ void __launch_bounds__(TOP_NT, sizeof(typename KT::T) == 4 ? 4 : 3)
 k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ vals,
           const uint16_t* __restrict__ bid, uint32_t n, int p, const uint32_t* __restrict__ col,
           const uint32_t* __restrict__ boff, typename KT::T* __restrict__ out, uint32_t* __restrict__ vout,

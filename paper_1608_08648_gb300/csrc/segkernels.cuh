@@ -403,7 +403,7 @@ size_t seg_scatter_smem(int maxp) {
 // k_scatter (stable with a payload).  Output buffer: out.
 // ---------------------------------------------------------------------------
 template <class KT, bool HV>
-__global__ void __launch_bounds__(SEG_NT, 3)
+__global__ void __launch_bounds__(SEG_NT, 4)
 k_seg_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ vals,
               const uint16_t* __restrict__ bid, const SegRec* __restrict__ rec, const uint32_t* __restrict__ tile0,
               uint32_t nseg, const SegTotals* __restrict__ tot, const uint32_t* __restrict__ col, int maxp,
