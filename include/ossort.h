@@ -43,8 +43,14 @@ extern "C" {
 #define OS_MAX_P   4096u               /* largest p accepted */
 #define OS_MAX_PS  (1u << 24)          /* largest p * s accepted */
 
-/* Key types. */
-typedef enum { OS_I32 = 0, OS_U64 = 1, OS_F64 = 2 } os_key_t;
+/* Key types.  OS_S32: 32-byte strings compared as memcmp does (unsigned bytes,
+ * lexicographic) -- the keys of the paper's experiments (Section 3).  A sort of
+ * OS_S32 keys partitions by the tagged order (first 8 bytes, tag), then orders
+ * the keys that tie on their first 8 (16, 24) bytes by the next 8; it reads a
+ * small count back from the device after each of those steps, so it
+ * synchronizes its stream, and it is not accepted by the batched sort or the
+ * server. */
+typedef enum { OS_I32 = 0, OS_U64 = 1, OS_F64 = 2, OS_S32 = 3 } os_key_t;
 
 /* Splitter choice: SqDet (Algorithm 1) or SqRan (Algorithm 2). */
 typedef enum { OS_DET = 0, OS_RAN = 1 } os_split_t;
@@ -97,7 +103,8 @@ typedef struct {
  *   max_bucket    : largest bucket |Y_j|.
  *   repart_keys   : keys moved by in-bucket repartitions, summed over levels
  *                   (every repartitioned key is read twice and written once).
- *   splitter_keys : p-1 keys of the key type (step 3), or unused when p_used = 1.
+ *   splitter_keys : p-1 keys of the key type (step 3; 32 bytes each for OS_S32),
+ *                   or unused when p_used = 1.
  *   splitter_tags : p-1 tags of the splitters (original position for OS_RAN,
  *                   position in the sorted-sequence concatenation for OS_DET).
  *   bucket_sizes  : p sizes |Y_j| (all of the input in bucket 0 when p_used = 1).

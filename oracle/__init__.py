@@ -20,8 +20,8 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _HDR = os.path.join(_HERE, "oracle.h")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 
-KT = {"i32": 0, "u64": 1, "f64": 2}
-NP_DT = {"i32": np.int32, "u64": np.uint64, "f64": np.float64}
+KT = {"i32": 0, "u64": 1, "f64": 2, "s32": 3}
+NP_DT = {"i32": np.int32, "u64": np.uint64, "f64": np.float64, "s32": np.uint8}
 SPLIT = {"det": 0, "ran": 1}
 
 _lib = None
@@ -53,6 +53,8 @@ def _load():
         lib.oracle_ran_index.argtypes = [u64, u64, u64]
         lib.oracle_key_cmp.restype = i32
         lib.oracle_key_cmp.argtypes = [i32, u64, u64]
+        lib.oracle_str_cmp.restype = i32
+        lib.oracle_str_cmp.argtypes = [ctypes.c_char_p, ctypes.c_char_p]
         lib.oracle_sort.restype = i32
         lib.oracle_sort.argtypes = [i32, vp, vp, u64, i32, u32, u32, u64,
                                     vp, vp, vp, vp, vp, vp]
@@ -76,6 +78,11 @@ def key_cmp(kt: str, a_bits: int, b_bits: int) -> int:
     return int(_load().oracle_key_cmp(KT[kt], a_bits, b_bits))
 
 
+def str_cmp(a: bytes, b: bytes) -> int:
+    assert len(a) == 32 and len(b) == 32
+    return int(_load().oracle_str_cmp(a, b))
+
+
 def _ptr(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
@@ -89,13 +96,16 @@ def sort(keys: np.ndarray, kt: str, split: str, p: int, s: int, seed: int = 0,
     (p entries) and ``p_used`` (p, or 1 when the input is too small to sample)."""
     lib = _load()
     keys = np.ascontiguousarray(keys, dtype=NP_DT[kt])
+    if kt == "s32":
+        keys = keys.reshape(-1, 32)     # n records of 32 bytes
     n = keys.shape[0]
     if vals is not None:
         vals = np.ascontiguousarray(vals, dtype=np.uint32)
         assert vals.shape[0] == n
-    out_k = np.empty(n, dtype=NP_DT[kt]) if merge else None
+    shape = (n, 32) if kt == "s32" else (n,)
+    out_k = np.empty(shape, dtype=NP_DT[kt]) if merge else None
     out_v = np.empty(n, dtype=np.uint32) if (merge and vals is not None) else None
-    spl_k = np.zeros(max(p - 1, 0), dtype=NP_DT[kt])
+    spl_k = np.zeros((max(p - 1, 0), 32) if kt == "s32" else max(p - 1, 0), dtype=NP_DT[kt])
     spl_t = np.zeros(max(p - 1, 0), dtype=np.uint64)
     sizes = np.zeros(p, dtype=np.uint64)
     p_used = ctypes.c_uint32(0)

@@ -78,15 +78,30 @@ int oracle_key_cmp(int kt, uint64_t a, uint64_t b) {
     return na ? -mag : mag;
 }
 
+/* 32-byte string keys (ORC_S32): a record holds the key's index into the input
+ * array, and keys compare as memcmp of their 32 bytes (unsigned bytes,
+ * lexicographic).  The input array of the sort being run: */
+static const unsigned char* g_str_keys = NULL;
+
+int oracle_str_cmp(const void* a, const void* b) {
+    const int c = memcmp(a, b, 32);
+    return (c > 0) - (c < 0);
+}
+
+static int key_cmp(int kt, uint64_t a, uint64_t b) {
+    if (kt == ORC_S32) return oracle_str_cmp(g_str_keys + 32 * a, g_str_keys + 32 * b);
+    return oracle_key_cmp(kt, a, b);
+}
+
 typedef struct {
-    uint64_t key;   /* raw bits of the key */
+    uint64_t key;   /* raw bits of the key (ORC_S32: its index in the input) */
     uint64_t tag;   /* duplicate-handling tag */
     uint32_t val;   /* payload */
 } rec_t;
 
 /* The tagged order of Section 2.2: key first, tag second. */
 static int rec_cmp(int kt, const rec_t* a, const rec_t* b) {
-    int c = oracle_key_cmp(kt, a->key, b->key);
+    int c = key_cmp(kt, a->key, b->key);
     if (c) return c;
     return (a->tag > b->tag) - (a->tag < b->tag);
 }
@@ -160,12 +175,14 @@ static int multiway_merge(int kt, run_t* runs, uint32_t q, rec_t* out) {
 
 /* ---- key I/O ------------------------------------------------------------------ */
 static uint64_t load_key(int kt, const void* k, uint64_t i) {
+    if (kt == ORC_S32) return i;
     if (kt == ORC_I32) return (uint64_t)((const uint32_t*)k)[i];
     return ((const uint64_t*)k)[i];
 }
 
 static void store_key(int kt, void* k, uint64_t i, uint64_t bits) {
-    if (kt == ORC_I32) ((uint32_t*)k)[i] = (uint32_t)bits;
+    if (kt == ORC_S32) memcpy((unsigned char*)k + 32 * i, g_str_keys + 32 * bits, 32);
+    else if (kt == ORC_I32) ((uint32_t*)k)[i] = (uint32_t)bits;
     else ((uint64_t*)k)[i] = bits;
 }
 
@@ -192,8 +209,9 @@ int oracle_sort(int kt, const void* keys, const uint32_t* vals, uint64_t n,
                 void* out_keys, uint32_t* out_vals,
                 void* spl_keys, uint64_t* spl_tags, uint64_t* bucket_sizes,
                 uint32_t* p_used) {
-    if (kt < ORC_I32 || kt > ORC_F64 || (split != ORC_DET && split != ORC_RAN)) return -1;
+    if (kt < ORC_I32 || kt > ORC_S32 || (split != ORC_DET && split != ORC_RAN)) return -1;
     if (p < 1 || s < 1 || (n > 0 && !keys)) return -1;
+    g_str_keys = kt == ORC_S32 ? (const unsigned char*)keys : NULL;
 
     rec_t* X = (rec_t*)malloc((n ? n : 1) * sizeof(rec_t));
     if (!X) return -2;

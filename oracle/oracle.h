@@ -19,7 +19,7 @@
 extern "C" {
 #endif
 
-enum { ORC_I32 = 0, ORC_U64 = 1, ORC_F64 = 2 };   /* key types */
+enum { ORC_I32 = 0, ORC_U64 = 1, ORC_F64 = 2, ORC_S32 = 3 };   /* key types; S32: 32-byte strings */
 enum { ORC_DET = 0, ORC_RAN = 1 };                /* splitter choice */
 
 /* SplitMix64 (Steele, Lea, Flood 2014) in counter form: the (i+1)-th output of the
@@ -39,8 +39,14 @@ uint64_t oracle_ran_index(uint64_t seed, uint64_t j, uint64_t n);
  * f64: IEEE 754 total order without NaN (sign first, then magnitude). */
 int oracle_key_cmp(int kt, uint64_t a_bits, uint64_t b_bits);
 
+/* Three-way compare of two 32-byte string keys: memcmp order (unsigned bytes,
+ * lexicographic), the order of the paper's experiments (Section 3). */
+int oracle_str_cmp(const void* a, const void* b);
+
 /*
- * SqDet / SqRan.  keys: n values of type kt; vals: n uint32 payloads or NULL.
+ * SqDet / SqRan.  keys: n values of type kt (ORC_S32: n records of 32 bytes);
+ * vals: n uint32 payloads or NULL.  Not reentrant for ORC_S32 (the key array
+ * is held in a file-scope pointer during the call).
  * p >= 1 sequences / buckets; s >= 1 is the regular oversampling factor r of
  * Algorithm 1 (DET) or the random oversampling factor s of Algorithm 2 (RAN).
  *

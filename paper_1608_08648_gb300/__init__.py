@@ -10,7 +10,7 @@ from __future__ import annotations
 
 import ctypes
 
-from .binding import (OS_DET, OS_F64, OS_I32, OS_OK, OS_RAN, OS_STABLE, OS_U64, os_check,  # noqa: F401
+from .binding import (OS_DET, OS_F64, OS_I32, OS_OK, OS_RAN, OS_S32, OS_STABLE, OS_U64, os_check,  # noqa: F401
                       os_graph_capture_segmented, os_graph_destroy, os_graph_kernels, os_graph_launch,
                       os_kernel_time, os_last_cuda_error, os_launch_count, os_params, os_profile_start,
                       os_profile_stop, os_read_counters, os_seg_class, os_seg_default_classes, os_seg_stats,
@@ -18,7 +18,7 @@ from .binding import (OS_DET, OS_F64, OS_I32, OS_OK, OS_RAN, OS_STABLE, OS_U64, 
                       os_sort_segmented, os_stats, os_strerror, os_tune_segmented, os_version, os_workspace_size,
                       os_workspace_size_host, os_workspace_size_segmented)
 
-KEY_TYPES = {"i32": OS_I32, "u64": OS_U64, "f64": OS_F64}
+KEY_TYPES = {"i32": OS_I32, "u64": OS_U64, "f64": OS_F64, "s32": OS_S32}
 SPLITS = {"det": OS_DET, "ran": OS_RAN}
 
 
@@ -39,7 +39,9 @@ def _key_type(t, key_type):
         return OS_F64
     if t.dtype in (torch.int64,) + ((torch.uint64,) if hasattr(torch, "uint64") else ()):
         return OS_U64
-    raise TypeError(f"unsupported key dtype {t.dtype}: int32, float64 or (u)int64")
+    if t.dtype == torch.uint8:
+        return OS_S32
+    raise TypeError(f"unsupported key dtype {t.dtype}: int32, float64, (u)int64 or uint8 (32-byte strings)")
 
 
 def params(split="ran", p=1024, s=16, seed=0, flags=OS_STABLE) -> os_params:
@@ -57,12 +59,18 @@ def workspace_bytes(n, key_type="i32", has_vals=False, split="ran", p=1024, s=16
 
 def sort(keys, values=None, *, split="ran", p=1024, s=16, seed=0, out=None, values_out=None, workspace=None,
          stream=None, key_type=None, stats=False):
-    """Sort a 1-D CUDA tensor of keys (int32, float64 or 64-bit unsigned held in int64/uint64),
-    optionally carrying an int32/uint32 payload, stably.  Returns (keys_out, values_out, stats)."""
+    """Sort a CUDA tensor of keys (1-D int32, float64 or 64-bit unsigned held in int64/uint64;
+    or uint8 of shape (n, 32): 32-byte strings in memcmp order), optionally carrying an
+    int32/uint32 payload, stably.  Returns (keys_out, values_out, stats)."""
     import torch
-    assert keys.is_cuda and keys.dim() == 1 and keys.is_contiguous()
+    assert keys.is_cuda and keys.is_contiguous()
     kt = _key_type(keys, key_type)
-    n = keys.numel()
+    if kt == OS_S32:
+        assert keys.dtype == torch.uint8 and keys.numel() % 32 == 0
+        n = keys.numel() // 32
+    else:
+        assert keys.dim() == 1
+        n = keys.numel()
     prm = params(split, p, s, seed)
     hv = values is not None
     if out is None:
@@ -82,7 +90,7 @@ def sort(keys, values=None, *, split="ran", p=1024, s=16, seed=0, out=None, valu
     st_struct = None
     if stats:
         import numpy as np
-        kb = 4 if kt == OS_I32 else 8
+        kb = {OS_I32: 4, OS_S32: 32}.get(kt, 8)
         spl_k = np.zeros(max(p - 1, 1) * kb, dtype=np.uint8)
         spl_t = np.zeros(max(p - 1, 1), dtype=np.uint64)
         sizes = np.zeros(p, dtype=np.uint64)
@@ -94,11 +102,12 @@ def sort(keys, values=None, *, split="ran", p=1024, s=16, seed=0, out=None, valu
     if rc != OS_OK:
         raise OssortError(rc)
     if stats:
-        dt = {OS_I32: np.int32, OS_U64: np.uint64, OS_F64: np.float64}[kt]
+        dt = {OS_I32: np.int32, OS_U64: np.uint64, OS_F64: np.float64, OS_S32: np.uint8}[kt]
         pu = int(st_struct.p_used)
+        sk = spl_k.view(dt).reshape(-1, 32) if kt == OS_S32 else spl_k.view(dt)
         info = {"p_used": pu, "depth": int(st_struct.depth), "max_bucket": int(st_struct.max_bucket),
                 "repart_keys": int(st_struct.repart_keys),
-                "spl_keys": spl_k.view(dt)[: (p - 1 if pu > 1 else 0)], "spl_tags": spl_t[: (p - 1 if pu > 1 else 0)],
+                "spl_keys": sk[: (p - 1 if pu > 1 else 0)], "spl_tags": spl_t[: (p - 1 if pu > 1 else 0)],
                 "bucket_sizes": sizes}
     return out, values_out, info
 

@@ -11,7 +11,7 @@ import os
 
 from . import build as _build
 
-OS_I32, OS_U64, OS_F64 = 0, 1, 2
+OS_I32, OS_U64, OS_F64, OS_S32 = 0, 1, 2, 3
 OS_DET, OS_RAN = 0, 1
 OS_OK, OS_ERR_ARG, OS_ERR_WS, OS_ERR_UNSUPPORTED, OS_ERR_CUDA, OS_ERR_DEVICE = range(6)
 OS_STABLE = 1

@@ -98,10 +98,10 @@ int num_sms_of_current_device() {
 
 namespace {
 
-size_t key_bytes(int kt) { return kt == OS_I32 ? 4 : 8; }
+size_t key_bytes(int kt) { return kt == OS_I32 ? 4 : (kt == OS_S32 ? 32 : 8); }
 
 int check_params(int kt, uint64_t n, const os_params* prm) {
-    if (kt < OS_I32 || kt > OS_F64 || !prm) return OS_ERR_ARG;
+    if (kt < OS_I32 || kt > OS_S32 || !prm) return OS_ERR_ARG;
     if (prm->split != OS_DET && prm->split != OS_RAN) return OS_ERR_ARG;
     if (prm->p < 1 || prm->s < 1) return OS_ERR_ARG;
     if (prm->flags & ~OS_STABLE) return OS_ERR_ARG;
@@ -114,6 +114,7 @@ int dispatch(int kt, RunArgs& a) {
     switch (kt) {
         case OS_I32: return run_i32(a);
         case OS_U64: return run_u64(a);
+        case OS_S32: return run_s32(a);
         default: return run_f64(a);
     }
 }
@@ -167,7 +168,10 @@ int fill_stats(int kt, const RunArgs& a, cudaStream_t st, os_stats* stats) {
             for (uint32_t j = 0; j + 1 < p; ++j) stats->splitter_tags[j] = t[j];
         }
         if (stats->splitter_keys) {
-            if (kt == OS_I32) {
+            if (kt == OS_S32) {
+                e = cudaMemcpy(stats->splitter_keys, a.res.str_keys, (size_t)(p - 1) * 32, cudaMemcpyDeviceToHost);
+                if (e != cudaSuccess) return cuda_fail(e);
+            } else if (kt == OS_I32) {
                 std::vector<uint32_t> o(p - 1);
                 e = cudaMemcpy(o.data(), a.res.spl_o, (p - 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost);
                 if (e != cudaSuccess) return cuda_fail(e);

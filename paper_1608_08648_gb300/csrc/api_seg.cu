@@ -61,6 +61,7 @@ int run_seg(int kt, SegArgs& a) {
 }
 
 int check_sizes(int kt, uint64_t n, uint32_t nseg, const SegClasses& cls) {
+    if (kt == OS_S32) return OS_ERR_UNSUPPORTED;
     if (kt < OS_I32 || kt > OS_F64) return OS_ERR_ARG;
     if (n > OS_MAX_N || nseg > OS_SEG_MAX_NSEG) return OS_ERR_UNSUPPORTED;
     const SegBounds b = seg_bounds_of(n, nseg, cls);
@@ -252,6 +253,7 @@ int os_tune_segmented(int key_type, const void* d_keys_in, void* d_keys_out, con
                       void* stream, uint32_t reps, os_seg_class* classes, uint32_t max_classes, uint32_t* nclass,
                       float* best_ms) {
     if (!h_seg_offsets || !classes || !nclass || max_classes < 1 || reps < 1 || nseg < 1) return OS_ERR_ARG;
+    if (key_type == OS_S32) return OS_ERR_UNSUPPORTED;
     if (key_type < OS_I32 || key_type > OS_F64) return OS_ERR_ARG;
     if (h_seg_offsets[0] != 0 || h_seg_offsets[nseg] != n) return OS_ERR_ARG;
     uint64_t max_len = 0;

@@ -389,6 +389,9 @@ struct TopResult {
     void* spl_o = nullptr;
     uint32_t* spl_t = nullptr;
     uint32_t* bsize = nullptr;
+    const uint32_t* det_index = nullptr;   // SqDet with a payload: payloads in the order of the sorted sequences
+    void* str_keys = nullptr;              // 32-byte keys: the splitters' keys (device)
+    const uint32_t* str_map = nullptr;
 };
 
 template <class KT, bool HV>
@@ -425,6 +428,7 @@ void sort_top(Ctx& c, const typename KT::T* kin, typename KT::T* kout, const uin
         uint32_t* vw2 = HV ? c.ar.take<uint32_t>(n) : nullptr;
         // Step 1: the p sequences sorted into w1 (stable).
         segment_sort<KT, HV>(c, SegSpec::even(p, n), kin, vin, w1, vw1, w2, vw2, internal_seed);
+        res.det_index = vw1;
         splitters_det<KT>(c, w1, n, p, s, internal_seed, spl_o, spl_t);
         partition_top<KT, HV>(c, w1, vw1, n, spl_o, spl_t, p, w2, vw2, boff, bsize);
         segment_sort<KT, HV>(c, SegSpec::offsets(boff, p, n), w2, vw2, kout, vout, w2, vw2, internal_seed);
@@ -472,5 +476,6 @@ int run_sort(RunArgs& a) {
 int run_i32(RunArgs& a);
 int run_u64(RunArgs& a);
 int run_f64(RunArgs& a);
+int run_s32(RunArgs& a);
 
 }  // namespace ossort

@@ -28,7 +28,7 @@ double now_s() {
     return duration<double>(steady_clock::now().time_since_epoch()).count();
 }
 
-size_t key_bytes_of(int kt) { return kt == OS_I32 ? 4 : 8; }
+size_t key_bytes_of(int kt) { return kt == OS_I32 ? 4 : (kt == OS_S32 ? 32 : 8); }
 
 constexpr uint32_t STATUS_WORDS = 8;   // pinned copy of a request's status block
 
@@ -156,6 +156,7 @@ void dispatch_loop(os_server_s* s) {
 
 int check_request(const os_request* req, size_t& ws_bytes) {
     if (!req || req->reserved != 0) return OS_ERR_ARG;
+    if (req->key_type == OS_S32) return OS_ERR_UNSUPPORTED;   // its sort synchronizes its stream
     if (req->n > 0 && !req->d_keys_in) return OS_ERR_ARG;
     return os_workspace_size(req->key_type, req->n, 0, &req->prm, &ws_bytes);
 }

@@ -49,6 +49,9 @@ S_REQKIND = 112
 S_REQLEN = 113
 S_REQOFF = 114
 S_REQSEED = 115
+S_STR = 121             # 121..124: the four words of a string
+S_STR_POOL = 131
+S_STR_PICK = 132
 
 DISTRIBUTIONS = ("uniform", "gaussian", "zero", "bucket", "staggered", "ggroup", "dup")
 
@@ -290,3 +293,41 @@ def serving_trace(count: int, rate: float = 2000.0, lo: int = 4096, hi: int = 1 
     return {"arrival_s": arrival.tolist(), "dtype": ["f64" if f else "i32" for f in is_f64],
             "dist": ["dup" if d else "uniform" for d in is_dup], "n": n.tolist(), "offset": off.tolist(),
             "req_seed": [int(x) & MASK64 for x in rseed.tolist()], "lo": lo, "hi": hi}
+
+
+STR_DISTRIBUTIONS = ("uniform", "dup", "prefix8", "prefix24", "ties16")
+
+
+def strings(dist: str, n: int, seed: int = 1, start: int = 0, count: int | None = None,
+            device="cpu") -> torch.Tensor:
+    """32-byte string keys as a uint8 tensor of shape (count, 32).
+
+    uniform : every byte uniform (the paper's workload, Section 3): word k of
+              string i is u(seed, S_STR + k, i), stored little-endian.
+    dup     : copies of 32 pool strings (pool word k of string j is
+              u(seed, S_STR_POOL, 4 j + k)), string i picks pool[u(seed, S_STR_PICK, i) mod 32].
+    prefix8 : the first 8 bytes equal for every string (pool word 0), the rest uniform.
+    prefix24: the first 24 bytes equal (pool words 0-2), the last 8 uniform.
+    ties16  : the first 16 bytes from one of 64 pool prefixes (picked as in dup),
+              the last 16 uniform."""
+    i = _positions(n, start, count, device)
+    words = [u64(seed, S_STR + k, i) for k in range(4)]
+    pool = u64(seed, S_STR_POOL, torch.arange(4 * 64, dtype=torch.int64, device=device)).view(64, 4)
+    if dist == "uniform":
+        pass
+    elif dist == "dup":
+        pick = _lsr(u64(seed, S_STR_PICK, i), 1) % 32
+        words = [pool[pick, k] for k in range(4)]
+    elif dist == "prefix8":
+        words[0] = pool[0, 0].expand_as(i)
+    elif dist == "prefix24":
+        for k in range(3):
+            words[k] = pool[0, k].expand_as(i)
+    elif dist == "ties16":
+        pick = _lsr(u64(seed, S_STR_PICK, i), 1) % 64
+        words[0] = pool[pick, 0]
+        words[1] = pool[pick, 1]
+    else:
+        raise ValueError(f"unknown string distribution {dist!r}")
+    w = torch.stack([x.contiguous() for x in words], dim=1).contiguous()     # (count, 4) int64
+    return w.view(torch.uint8).view(-1, 32)
