@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -48,9 +49,10 @@ def parse():
     ap.add_argument("--ref-sample", type=int, default=1 << 20, help="keys per step of --impl reference")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="sort", choices=["sort", "batched", "serving"],
+    ap.add_argument("--workload", default="sort", choices=["sort", "batched", "serving", "strings"],
                     help="sort: one array (the headline line, with 'batched' and 'serving' summaries); batched / "
-                         "serving: that workload as the line's own metric")
+                         "serving / strings (the paper's 32-byte keys, Table 1 grid): that workload as the "
+                         "line's own metric")
     ap.add_argument("--no-batched", action="store_true", help="leave the batched summary out of the sort line")
     ap.add_argument("--no-serving", action="store_true", help="leave the serving summary out of the sort line")
     ap.add_argument("--requests", type=int, default=20000, help="serving: requests of the replayed trace")
@@ -526,6 +528,164 @@ def run_serving_line(a, rank, world, local):
     return res
 
 
+# ---- the paper's workload: 32-byte random strings ---------------------------------------
+
+STR_GRID_N = (1_024_000, 4_096_000, 8_192_000, 16_384_000, 32_768_000)
+STR_GRID_P = (4, 32, 64, 128, 256)
+# Table 1 of the paper, SqRan(qsort) on one Xeon E3-1240 core, seconds (context only)
+PAPER_T1_SQRAN_S = {(32_768_000, 256): 11.48, (8_192_000, 256): 2.61}
+
+
+def str_default_s(n):
+    return int(math.ceil(math.log2(n) ** 2))
+
+
+def str_alg_bytes(name, n):
+    """Bytes per string sort a kernel must move: the method's kernels move (8-byte word,
+    4-byte index) pairs; k_str_init reads the 32-byte keys and writes the pairs;
+    k_str_gather reads the indices and the keys and writes the keys."""
+    if name == "k_str_init":
+        return n * (32 + 12)
+    if name == "k_str_gather":
+        return n * (4 + 32 + 32)
+    return algorithmic_bytes(name, n, 8, 4, 0)
+
+
+def run_strings_line(a, rank, world, local):
+    import torch
+
+    import paper_1608_08648_gb300 as oss
+    from paper_1608_08648_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    grid = []
+    nmax = max(STR_GRID_N)
+    keys_all = inputs.strings("uniform", nmax, seed=a.seed + rank, device=dev)
+    out_all = torch.empty_like(keys_all)
+
+    def time_one(n, p, s, steps, warmup, profile=False):
+        keys = keys_all[:n]
+        out = out_all[:n]
+        prm = oss.params("ran", p, s, a.seed)
+        rc, need = oss.os_workspace_size(oss.OS_S32, n, False, prm)
+        assert rc == 0, oss.os_strerror(rc)
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+
+        def step():
+            r = oss.os_sort(oss.OS_S32, keys.data_ptr(), out.data_ptr(), None, None, n, prm, ws.data_ptr(), need, sh,
+                            None)
+            if r != 0:
+                raise RuntimeError(f"os_sort failed: {oss.os_strerror(r)}")
+
+        for _ in range(warmup):
+            step()
+        rc, bits = oss.os_check(ws.data_ptr(), sh)
+        assert rc == 0 and bits == 0
+        prof = None
+        if profile:
+            oss.os_profile_start()
+        l0 = oss.os_launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = oss.os_launch_count() - l0
+        if profile:
+            _, prof = oss.os_profile_stop()
+        return e0.elapsed_time(e1) / steps, launches, prof, out
+
+    for n in STR_GRID_N:
+        for p in STR_GRID_P:
+            s = str_default_s(n)
+            ms, _, _, _ = time_one(n, p, s, 2, 1)
+            row = {"n": n, "p": p, "s": s, "ms": round(ms, 3), "keys_per_s": n / (ms / 1e3)}
+            if (n, p) in PAPER_T1_SQRAN_S:
+                row["paper_sqran_qs_s"] = PAPER_T1_SQRAN_S[(n, p)]
+                row["speedup_vs_paper"] = round(PAPER_T1_SQRAN_S[(n, p)] / (ms / 1e3), 1)
+            grid.append(row)
+    # the headline point: n = 32,768,000, p = 256, s = ceil(lg^2 n), timed with clocks and the profiler
+    n, p = 32_768_000, 256
+    s = str_default_s(n)
+    clocks = Clocks(local)
+    barrier(world)
+    clocks.start()
+    time.sleep(0.3)
+    ms, launches, _, out = time_one(n, p, s, a.steps, a.warmup)
+    clk = clocks.stop()
+    ms = max_over_ranks(ms, world)
+    # correctness of the timed output: ordered (big-endian words)
+    w = out.view(n, 4, 8).flip(2).contiguous().view(torch.int64).view(n, 4) ^ (-(1 << 63))
+    lt = torch.zeros(n - 1, dtype=torch.bool, device=dev)
+    eq = torch.ones(n - 1, dtype=torch.bool, device=dev)
+    for k in range(4):
+        lt |= eq & (w[:-1, k] < w[1:, k])
+        eq &= w[:-1, k] == w[1:, k]
+    assert bool((lt | eq).all()), "strings out of order"
+    del w, lt, eq
+    _, _, prof, _ = time_one(n, p, s, 2, 0, profile=True)
+    peaks, peak_kind = measured_peaks()
+    top = [k for k in prof if not k["name"].endswith(".sample")]
+    dom = max(top, key=lambda k: k["total_ms"])
+    alg = str_alg_bytes(dom["name"], n)
+    achieved = alg / (dom["total_ms"] / dom["launches"] / 1e3) / 1e9 if dom["total_ms"] > 0 else 0.0
+    roof = {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1), "peak": float(peaks["hbm_gbs"]),
+            "unit": "GB/s", "frac": round(achieved / float(peaks["hbm_gbs"]), 4), "traffic": None,
+            "peak_source": f"{peak_kind} hbm_gbs", "avg_launch_ms": round(dom["total_ms"] / dom["launches"], 4),
+            "alg_bytes_per_step": alg}
+    e2e = None
+    if not a.no_e2e:
+        prm = oss.params("ran", p, s, a.seed)
+        h_in = keys_all[:n].cpu().pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        rc, hneed = oss.os_workspace_size_host(oss.OS_S32, n, False, prm)
+        hws = torch.empty(hneed, dtype=torch.uint8, device=dev)
+        r = oss.os_sort_host(oss.OS_S32, h_in.data_ptr(), h_out.data_ptr(), None, None, n, prm, hws.data_ptr(),
+                             hneed, sh)
+        assert r == 0
+        t0 = time.perf_counter()
+        k2 = 3
+        for _ in range(k2):
+            r = oss.os_sort_host(oss.OS_S32, h_in.data_ptr(), h_out.data_ptr(), None, None, n, prm, hws.data_ptr(),
+                                 hneed, sh)
+            assert r == 0
+        t = max_over_ranks((time.perf_counter() - t0) / k2, world)
+        assert torch.equal(h_out, out.cpu())
+        e2e = {"value": world * n / t, "unit": "keys/s", "ms_per_step": t * 1e3, "h2d_bytes_per_step": n * 32,
+               "d2h_bytes_per_step": n * 32}
+    value = world * n / (ms / 1e3)
+    res = {"metric": "keys/s (32-byte strings, memcmp order)", "value": value, "unit": "keys/s", "n_gpus": world,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": value / (32_768_000 / PAPER_T1_SQRAN_S[(32_768_000, 256)]),
+           "vs_baseline_note": "against Table 1 of the paper: SqRan(qsort), n = 32,768,000, p = 256, default s, "
+                               "11.48 s on one core of a Xeon E3-1240 (other hardware: context only)",
+           "dtype": "s32", "data": "synthetic",
+           "config": {"workload": f"n={n} random 32-byte strings (uniform bytes), memcmp order, SqRan p={p} "
+                                  f"s=ceil(lg^2 n)={s}, seed {a.seed}", "n": n, "p": p, "s": s,
+                      "l2": "inputs larger than L2 (no flush needed)", "parallelism": "replicas"},
+           "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "grid": grid,
+           "kernels": [{"name": k["name"], "launches": k["launches"], "total_ms": round(k["total_ms"], 4)}
+                       for k in sorted(prof, key=lambda k: -k["total_ms"])[:12]]}
+    if rank == 0 and world == 1 and not a.no_cpu:
+        import numpy as np
+
+        import oracle
+        m = min(a.cpu_sample, 1 << 22)
+        kh = keys_all[:m].cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.sort(kh, "s32", "ran", p, str_default_s(m), seed=a.seed)
+        t = time.perf_counter() - t0
+        res["cpu_baseline"] = {"value": m / t, "unit": "keys/s", "cores": 1, "kind": "oracle",
+                               "host_cores": cpu_cores(),
+                               "sample": f"the first {m} strings, one oracle run ({t:.2f} s)"}
+    return res
+
+
 # ---- our arm ------------------------------------------------------------------------
 
 def run_ours(a, rank, world, local):
@@ -744,6 +904,26 @@ def run_reference(a, rank, world):
     from paper_1608_08648_gb300 import inputs
     if rank != 0:
         return None
+    if a.workload == "strings":
+        n = 32_768_000
+        m = min(a.ref_sample, n)
+        keys = inputs.strings("uniform", n, seed=a.seed, count=m).numpy()
+        for _ in range(a.warmup):
+            oracle.sort(keys, "s32", "ran", 256, str_default_s(m), seed=a.seed)
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            oracle.sort(keys, "s32", "ran", 256, str_default_s(m), seed=a.seed)
+        t = (time.perf_counter() - t0) / a.steps
+        v = m / t
+        return {"impl": "reference", "metric": "keys/s (32-byte strings, memcmp order)", "value": v,
+                "unit": "keys/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "s32",
+                "data": "synthetic",
+                "config": {"workload": f"n={n} random 32-byte strings, SqRan p=256 s=ceil(lg^2 n)",
+                           "parallelism": "replicas"},
+                "cpu_baseline": {"value": v, "unit": "keys/s", "kind": "oracle", "cores": 1,
+                                 "sample": f"the first {m} strings per step"},
+                "e2e": {"value": v, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     if a.workload == "serving":
         import numpy as np
         tr = inputs.serving_trace(a.requests, a.rate, SERVE["lo"], SERVE["hi"], seed=SERVE["seed"])
@@ -832,6 +1012,8 @@ def main():
             res = run_batched_line(a, rank, world, local)
         elif a.workload == "serving":
             res = run_serving_line(a, rank, world, local)
+        elif a.workload == "strings":
+            res = run_strings_line(a, rank, world, local)
         else:
             res = run_ours(a, rank, world, local)
     if rank == 0 and res is not None:

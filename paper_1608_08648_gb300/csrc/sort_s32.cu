@@ -36,6 +36,10 @@ int run_s32(RunArgs& a) {
     uint32_t* seg = c.ar.take<uint32_t>((size_t)n / 2 + 2);
     const size_t sub_bytes = str_refine_bytes(n);
     char* sub = c.ar.take<char>(sub_bytes);
+    // In place (in == out, as os_sort_host sorts): the gather goes through a copy.
+    const bool in_place = a.kin == a.kout;
+    Str32* tmp = c.ar.take<Str32>(in_place ? n : 0);
+    uint32_t* vtmp = c.ar.take<uint32_t>(in_place && a.has_vals ? n : 0);
     a.res.str_keys = c.ar.take<Str32>(std::max<uint32_t>(a.prm.p, 2) - 1);
     a.res.str_map = a.prm.split == OS_DET ? a.res.det_index : nullptr;
     a.used = c.ar.used;
@@ -66,7 +70,15 @@ int run_s32(RunArgs& a) {
         if (sc.ar.failed) return OS_ERR_WS;
         OS_LAUNCH(c.st, "k_str_put", k_str_put<<<grid_for(h_tot[0], 256), 256, 0, c.st>>>(Iw2, pos, tot, Is));
     }
-    OS_LAUNCH(c.st, "k_str_gather", k_str_gather<<<g, 256, 0, c.st>>>(in, a.vin, Is, n, out, a.vout));
+    if (in_place) {
+        OS_LAUNCH(c.st, "k_str_gather", k_str_gather<<<g, 256, 0, c.st>>>(in, a.vin, Is, n, tmp, vtmp));
+        cudaError_t err = cudaMemcpyAsync(out, tmp, (size_t)n * sizeof(Str32), cudaMemcpyDeviceToDevice, c.st);
+        if (err == cudaSuccess && a.has_vals)
+            err = cudaMemcpyAsync(a.vout, vtmp, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, c.st);
+        if (err != cudaSuccess) return OS_ERR_CUDA;
+    } else {
+        OS_LAUNCH(c.st, "k_str_gather", k_str_gather<<<g, 256, 0, c.st>>>(in, a.vin, Is, n, out, a.vout));
+    }
     if (a.res.p_used > 1)
         OS_LAUNCH(c.st, "k_str_splitters",
                   k_str_splitters<<<grid_for(a.res.p_used - 1, 256), 256, 0, c.st>>>(

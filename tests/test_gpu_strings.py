@@ -84,3 +84,24 @@ def test_full_size_paper_workload_properties():
     # ties (if any) keep input order
     assert bool((~eq | (vout[1:] > vout[:-1])).all())
     assert st["p_used"] == 256 and int(st["bucket_sizes"].sum()) == n
+
+
+def test_in_place_and_host_buffers():
+    n = 100_003
+    keys = inputs.strings("prefix8", n, seed=8, device="cuda")
+    vals = torch.arange(n, dtype=torch.int32, device="cuda")
+    ref_k, ref_v, _ = oss.sort(keys, vals, split="ran", p=32, s=8, seed=8, key_type="s32")
+    k2, v2 = keys.clone(), vals.clone()
+    oss.sort(k2, v2, split="ran", p=32, s=8, seed=8, key_type="s32", out=k2, values_out=v2)
+    torch.cuda.synchronize()
+    assert torch.equal(k2, ref_k) and torch.equal(v2, ref_v)
+    # the host-buffer entry point sorts in place inside its workspace
+    prm = oss.params("ran", 32, 8, 8)
+    rc, need = oss.os_workspace_size_host(oss.OS_S32, n, False, prm)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    h_in = keys.cpu().pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    rc = oss.os_sort_host(oss.OS_S32, h_in.data_ptr(), h_out.data_ptr(), None, None, n, prm, ws.data_ptr(), need,
+                          torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    assert torch.equal(h_out, ref_k.cpu())
