@@ -572,10 +572,10 @@ def run_strings_line(a, rank, world, local):
     keys_all = inputs.strings("uniform", nmax, seed=a.seed + rank, device=dev)
     out_all = torch.empty_like(keys_all)
 
-    def time_one(n, p, s, steps, warmup, profile=False):
+    def time_one(n, p, s, steps, warmup, profile=False, split="ran"):
         keys = keys_all[:n]
         out = out_all[:n]
-        prm = oss.params("ran", p, s, a.seed)
+        prm = oss.params(split, p, s, a.seed)
         rc, need = oss.os_workspace_size(oss.OS_S32, n, False, prm)
         assert rc == 0, oss.os_strerror(rc)
         ws = torch.empty(need, dtype=torch.uint8, device=dev)
@@ -616,6 +616,20 @@ def run_strings_line(a, rank, world, local):
                 row["paper_sqran_qs_s"] = PAPER_T1_SQRAN_S[(n, p)]
                 row["speedup_vs_paper"] = round(PAPER_T1_SQRAN_S[(n, p)] / (ms / 1e3), 1)
             grid.append(row)
+    # Table 2 of the paper: SqRan, n = 8,192,000, p = 256, s = ceil(lg^(1+a) n); Table 8: SqDet,
+    # n = 8,192,000, p = 128, regular oversampling r = 1..5
+    sweeps = []
+    if not a.no_grid:
+        n2 = 8_192_000
+        for aa in (0.2, 0.6, 1.0, 1.4, 1.8):
+            s2 = int(math.ceil(math.log2(n2) ** (1 + aa)))
+            ms2, _, _, _ = time_one(n2, 256, s2, 2, 1)
+            sweeps.append({"table": 2, "split": "ran", "n": n2, "p": 256, "a": aa, "s": s2, "ms": round(ms2, 3),
+                           "keys_per_s": n2 / (ms2 / 1e3)})
+        for r in (1, 2, 3, 4, 5):
+            ms2, _, _, _ = time_one(n2, 128, r, 2, 1, split="det")
+            sweeps.append({"table": 8, "split": "det", "n": n2, "p": 128, "r": r, "ms": round(ms2, 3),
+                           "keys_per_s": n2 / (ms2 / 1e3)})
     # the headline point: n = 32,768,000, p = 256, s = ceil(lg^2 n), timed with clocks and the profiler
     n, p = 32_768_000, 256
     s = str_default_s(n)
@@ -675,7 +689,7 @@ def run_strings_line(a, rank, world, local):
            "config": {"workload": f"n={n} random 32-byte strings (uniform bytes), memcmp order, SqRan p={p} "
                                   f"s=ceil(lg^2 n)={s}, seed {a.seed}", "n": n, "p": p, "s": s,
                       "l2": "inputs larger than L2 (no flush needed)", "parallelism": "replicas"},
-           "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "grid": grid,
+           "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "grid": grid, "sweeps": sweeps,
            "kernels": [{"name": k["name"], "launches": k["launches"], "total_ms": round(k["total_ms"], 4)}
                        for k in sorted(prof, key=lambda k: -k["total_ms"])[:12]]}
     if rank == 0 and world == 1 and not a.no_cpu:
