@@ -263,9 +263,11 @@ size_t classify_smem(int p, int lbits) {
 template <class KT, bool HV>
 size_t scatter_smem(int p) {
     using T = typename KT::T;
-    size_t b = sizeof(T) * TOP_TILE + (HV ? sizeof(uint32_t) * TOP_TILE : 0);
+    using SC = ScatterCfg<T, HV>;
+    constexpr int SUB = SC::SUB;
+    size_t b = sizeof(T) * SUB + (HV ? sizeof(uint32_t) * SUB : 0);
     b += sizeof(uint32_t) * (p + 1) + sizeof(uint32_t) * p + sizeof(uint32_t) * 32;
-    b += sizeof(uint16_t) * TOP_TILE + (HV ? sizeof(uint16_t) * TOP_WARPS * (p + 1) : 0);
+    b += sizeof(uint16_t) * SUB + (HV ? sizeof(uint16_t) * SC::WARPS * (p + 1) : 0);
     return b;
 }
 
@@ -277,24 +279,25 @@ void partition_top(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, uint
                    const typename KT::O* spl_o, const uint32_t* spl_t, uint32_t p, typename KT::T* dst,
                    uint32_t* vdst, uint32_t* boff, uint32_t* bsize) {
     const int lb = table_lbits(p);
-    const uint32_t ntiles = (n + TOP_TILE - 1) / TOP_TILE;
+    const uint32_t ntiles = (n + TOP_SUPER - 1) / TOP_SUPER;
     const uint32_t gmax = std::min<uint32_t>(std::max<uint32_t>(ntiles, 1), G_CAP);
     uint32_t* hist = c.ar.take<uint32_t>((size_t)p * gmax);
     uint32_t* col = c.ar.take<uint32_t>((size_t)p * gmax);
     uint16_t* bid = c.ar.take<uint16_t>(n);
     if (!c.live()) return;
+    constexpr int NTS = ScatterCfg<typename KT::T, HV>::NT;
     const size_t sm_c = classify_smem<KT>(p, lb), sm_s = scatter_smem<KT, HV>(p);
-    cudaFuncSetAttribute(k_classify<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c);
+    cudaFuncSetAttribute(k_classify<KT, NTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c);
     cudaFuncSetAttribute(k_scatter<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_s);
-    const int occ = occupancy(k_scatter<KT, HV>, TOP_NT, sm_s);
+    const int occ = occupancy(k_scatter<KT, HV>, NTS, sm_s);
     const uint32_t G = std::max<uint32_t>(1, std::min<uint32_t>(gmax, (uint32_t)(c.num_sms * occ)));
     OS_LAUNCH(c.st, c.nested ? "k_classify.sample" : "k_classify",
-              k_classify<KT><<<G, TOP_NT, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, lb, hist, bid, ntiles));
+              k_classify<KT, NTS><<<G, NTS, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, lb, hist, bid, ntiles));
     OS_LAUNCH(c.st, c.nested ? "k_column_scan.sample" : "k_column_scan",
               k_column_scan<<<grid_for((uint64_t)p * 32, 256), 256, 0, c.st>>>(hist, p, G, col, bsize));
     OS_LAUNCH(c.st, c.nested ? "k_bucket_offsets.sample" : "k_bucket_offsets", k_bucket_offsets<<<1, 1024, 0, c.st>>>(bsize, p, boff));
     OS_LAUNCH(c.st, c.nested ? "k_scatter.sample" : "k_scatter",
-              k_scatter<KT, HV><<<G, TOP_NT, sm_s, c.st>>>(src, vsrc, bid, n, (int)p, col, boff, dst, vdst,
+              k_scatter<KT, HV><<<G, NTS, sm_s, c.st>>>(src, vsrc, bid, n, (int)p, col, boff, dst, vdst,
                                                            ntiles, c.status));
 }
 

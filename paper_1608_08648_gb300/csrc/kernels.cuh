@@ -117,17 +117,18 @@ __global__ void k_pick_splitters(const typename KT::T* __restrict__ tk, const ui
 }
 
 // ---------------------------------------------------------------------------
-// Step 4, pass 1: every CTA owns a contiguous run of tiles, finds the bucket of
-// each key (tag = its position in the array), stores it in bid (two bytes a
-// key, read back by the scatter instead of searching again) and counts keys
-// per bucket.  hist is bucket-major: hist[b * G + g].
+// Step 4, pass 1: every CTA owns a contiguous run of units of TOP_SUPER keys
+// (the scatter's tiles, walked here as halves), finds the bucket of each key
+// (tag = its position in the array), stores it in bid (two bytes a key, read
+// back by the scatter instead of searching again) and counts keys per bucket.
+// hist is bucket-major: hist[b * G + g].
 // ---------------------------------------------------------------------------
 __host__ __device__ inline uint32_t tile_lo(uint32_t g, uint32_t G, uint32_t ntiles) {
     return (uint32_t)(((uint64_t)g * ntiles) / G);
 }
 
-template <class KT>
-__global__ void __launch_bounds__(TOP_NT, 3)
+template <class KT, int NT>
+__global__ void __launch_bounds__(NT, NT == 512 ? 2 : 3)
 k_classify(const typename KT::T* __restrict__ keys, uint32_t n, const typename KT::O* __restrict__ spl_o,
            const uint32_t* __restrict__ spl_t, int p, int lbits, uint32_t* __restrict__ hist,
            uint16_t* __restrict__ bid, uint32_t ntiles) {
@@ -136,15 +137,16 @@ k_classify(const typename KT::T* __restrict__ keys, uint32_t n, const typename K
     SplitTable<O> tb;
     tb.bind(smem, p - 1, lbits);
     uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + split_table_bytes<O>(p - 1, lbits));   // [p + 1]
-    for (int i = threadIdx.x; i < p - 1; i += TOP_NT) tb.set(i, spl_o[i], spl_t[i]);
-    for (int b = threadIdx.x; b <= p; b += TOP_NT) cnt[b] = 0;
+    for (int i = threadIdx.x; i < p - 1; i += NT) tb.set(i, spl_o[i], spl_t[i]);
+    for (int b = threadIdx.x; b <= p; b += NT) cnt[b] = 0;
     __syncthreads();
     split_table_finish<O>(tb, p - 1, lbits);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t G = gridDim.x, g = blockIdx.x;
     const uint32_t t0 = tile_lo(g, G, ntiles), t1 = tile_lo(g + 1, G, ntiles);
-    for (uint32_t t = t0; t < t1; ++t) {
-        const uint32_t base = t * TOP_TILE + w * (TOP_IT * 32) + lane;
+    constexpr int SUB = NT * TOP_IT;
+    for (uint32_t th = t0 * (TOP_SUPER / SUB); th < t1 * (TOP_SUPER / SUB); ++th) {
+        const uint32_t base = th * SUB + w * (TOP_IT * 32) + lane;
         O o[TOP_IT];
 #pragma unroll
         for (int i = 0; i < TOP_IT; ++i) {
@@ -164,7 +166,7 @@ k_classify(const typename KT::T* __restrict__ keys, uint32_t n, const typename K
         }
     }
     __syncthreads();
-    for (int b = threadIdx.x; b < p; b += TOP_NT) hist[(size_t)b * G + g] = cnt[b];
+    for (int b = threadIdx.x; b < p; b += NT) hist[(size_t)b * G + g] = cnt[b];
 }
 
 // Exclusive scan of every bucket's column of CTA counts (one warp per bucket),
@@ -204,8 +206,10 @@ static __global__ void k_bucket_offsets(const uint32_t* __restrict__ bsize, uint
 }
 
 // ---------------------------------------------------------------------------
-// Step 4, pass 2: the same CTAs walk the same tiles in order and move the keys
-// (and payloads) into their buckets, using the bucket ids of pass 1.  Keys are
+// Step 4, pass 2: the same CTAs walk the same key ranges in tiles of TOP_SUPER
+// keys (512 threads; longer runs per bucket than pass 1's halves, so fewer
+// partly written 32-byte sectors) and move the keys (and payloads) into their
+// buckets, using the bucket ids of pass 1.  Keys are
 // staged in shared memory grouped by bucket and written out as contiguous runs.
 // With a payload the scatter is stable: a key's rank among the tile's keys of
 // its bucket comes from per-warp counters (peer masks from ballots) plus a
@@ -214,31 +218,34 @@ static __global__ void k_bucket_offsets(const uint32_t* __restrict__ bsize, uint
 // shared-memory atomics, one per run of equal neighbours, hand out the slots.
 // ---------------------------------------------------------------------------
 template <class KT, bool HV>
-__global__ void __launch_bounds__(TOP_NT, sizeof(typename KT::T) == 4 ? 4 : 3)
+__global__ void __launch_bounds__(ScatterCfg<typename KT::T, HV>::NT, ScatterCfg<typename KT::T, HV>::NT == 512 ? 2
+                                  : (sizeof(typename KT::T) == 4 ? 4 : 3))
 k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ vals,
           const uint16_t* __restrict__ bid, uint32_t n, int p, const uint32_t* __restrict__ col,
           const uint32_t* __restrict__ boff, typename KT::T* __restrict__ out, uint32_t* __restrict__ vout,
           uint32_t ntiles, uint32_t* status) {
     using T = typename KT::T;
+    using SC = ScatterCfg<typename KT::T, HV>;
+    constexpr int SNT = SC::NT, SWARPS = SC::WARPS, SUB = SC::SUB;
     extern __shared__ __align__(16) char smem[];
     char* q = smem;
-    T* sk = reinterpret_cast<T*>(q);                 q += sizeof(T) * TOP_TILE;
-    uint32_t* sv = reinterpret_cast<uint32_t*>(q);    q += HV ? sizeof(uint32_t) * TOP_TILE : 0;
+    T* sk = reinterpret_cast<T*>(q);                 q += sizeof(T) * SUB;
+    uint32_t* sv = reinterpret_cast<uint32_t*>(q);    q += HV ? sizeof(uint32_t) * SUB : 0;
     uint32_t* tile_off = reinterpret_cast<uint32_t*>(q); q += sizeof(uint32_t) * (p + 1);
     uint32_t* cursor = reinterpret_cast<uint32_t*>(q);   q += sizeof(uint32_t) * p;
     uint32_t* scratch = reinterpret_cast<uint32_t*>(q);  q += sizeof(uint32_t) * 32;
-    uint16_t* sb = reinterpret_cast<uint16_t*>(q);       q += sizeof(uint16_t) * TOP_TILE;
-    uint16_t* cnt = reinterpret_cast<uint16_t*>(q);      // HV: [TOP_WARPS][p + 1]
+    uint16_t* sb = reinterpret_cast<uint16_t*>(q);       q += sizeof(uint16_t) * SUB;
+    uint16_t* cnt = reinterpret_cast<uint16_t*>(q);      // HV: [SWARPS][p + 1]
     const int cstride = p + 1;
 
     const uint32_t G = gridDim.x, g = blockIdx.x;
-    for (int b = threadIdx.x; b < p; b += TOP_NT) cursor[b] = boff[b] + col[(size_t)b * G + g];
+    for (int b = threadIdx.x; b < p; b += SNT) cursor[b] = boff[b] + col[(size_t)b * G + g];
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint16_t* mycnt = cnt + w * cstride;
     const uint32_t t0 = tile_lo(g, G, ntiles), t1 = tile_lo(g + 1, G, ntiles);
-    for (uint32_t t = t0; t < t1; ++t) {
-        const uint32_t tbase = t * TOP_TILE;
+    for (uint32_t t = t0 * (TOP_SUPER / SUB); t < t1 * (TOP_SUPER / SUB); ++t) {   // tiles of SUB keys
+        const uint32_t tbase = t * SUB;
         const uint32_t base = tbase + w * (TOP_IT * 32) + lane;
         T kv[TOP_IT];
         uint32_t br[TOP_IT];   // bucket << 16 | rank inside the tile's part of the bucket
@@ -251,7 +258,7 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
         if (HV) {
             for (int b = lane; b <= p; b += 32) mycnt[b] = 0;
         } else {
-            for (int b = threadIdx.x; b <= p; b += TOP_NT) tile_off[b] = 0;
+            for (int b = threadIdx.x; b <= p; b += SNT) tile_off[b] = 0;
         }
         __syncthreads();   // counters cleared; previous tile fully written out
         if (HV) {
@@ -268,10 +275,10 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
             }
             __syncthreads();
             // Cross-warp exclusive prefix per bucket; tile totals into tile_off.
-            for (int b = threadIdx.x; b < p; b += TOP_NT) {
+            for (int b = threadIdx.x; b < p; b += SNT) {
                 uint32_t run = 0;
 #pragma unroll
-                for (int ww = 0; ww < TOP_WARPS; ++ww) {
+                for (int ww = 0; ww < SWARPS; ++ww) {
                     const uint32_t c = cnt[ww * cstride + b];
                     cnt[ww * cstride + b] = (uint16_t)run;
                     run += c;
@@ -293,7 +300,7 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
             const int b = (int)(br[i] >> 16);
             if (b < p) {
                 const uint32_t loc = tile_off[b] + (HV ? mycnt[b] : 0u) + (br[i] & 0xFFFFu);
-                if (loc >= (uint32_t)TOP_TILE) {
+                if (loc >= (uint32_t)SUB) {
                     flag_bounds(status, 8, loc);
                     continue;
                 }
@@ -303,7 +310,7 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
             }
         }
         __syncthreads();
-        for (uint32_t j = threadIdx.x; j < tvalid; j += TOP_NT) {
+        for (uint32_t j = threadIdx.x; j < tvalid; j += SNT) {
             const int b = sb[j];
             const uint32_t dst = cursor[b] + (j - tile_off[b]);
             if (dst >= n) {
@@ -314,7 +321,7 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
             if (HV) vout[dst] = sv[j];
         }
         __syncthreads();
-        for (int b = threadIdx.x; b < p; b += TOP_NT) cursor[b] += tile_off[b + 1] - tile_off[b];
+        for (int b = threadIdx.x; b < p; b += SNT) cursor[b] += tile_off[b + 1] - tile_off[b];
         __syncthreads();   // tile_off is cleared at the top of the next tile
     }
 }
