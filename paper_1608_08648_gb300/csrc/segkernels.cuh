@@ -388,12 +388,21 @@ k_seg_scan(const SegRec* __restrict__ rec, uint32_t nseg, const SegTotals* __res
     }
 }
 
+// Scatter staging: 256 threads stage 2048 keys at a time (measured on GB300: 512
+// threads staging 4096 keys were slower for the bucket phase's ~90 children).
+template <bool HV> struct SegScatterCfg {
+    static constexpr int NT = SEG_NT;
+    static constexpr int WARPS = NT / 32;
+    static constexpr int SUB = NT * SEG_IT;
+};
+
 template <class KT, bool HV>
 size_t seg_scatter_smem(int maxp) {
     using T = typename KT::T;
-    size_t b = sizeof(T) * SEG_SUB + (HV ? sizeof(uint32_t) * SEG_SUB : 0);
+    using SC = SegScatterCfg<HV>;
+    size_t b = sizeof(T) * SC::SUB + (HV ? sizeof(uint32_t) * SC::SUB : 0);
     b += sizeof(uint32_t) * (maxp + 1) + sizeof(uint32_t) * maxp + sizeof(uint32_t) * 32;
-    b += sizeof(uint16_t) * SEG_SUB + (HV ? sizeof(uint16_t) * SEG_WARPS * (maxp + 1) : 0);
+    b += sizeof(uint16_t) * SC::SUB + (HV ? sizeof(uint16_t) * SC::WARPS * (maxp + 1) : 0);
     return b;
 }
 
@@ -403,21 +412,22 @@ size_t seg_scatter_smem(int maxp) {
 // k_scatter (stable with a payload).  Output buffer: out.
 // ---------------------------------------------------------------------------
 template <class KT, bool HV>
-__global__ void __launch_bounds__(SEG_NT, 4)
+__global__ void __launch_bounds__(SegScatterCfg<HV>::NT, 4)
 k_seg_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ vals,
               const uint16_t* __restrict__ bid, const SegRec* __restrict__ rec, const uint32_t* __restrict__ tile0,
               uint32_t nseg, const SegTotals* __restrict__ tot, const uint32_t* __restrict__ col, int maxp,
               typename KT::T* __restrict__ out, uint32_t* __restrict__ vout, uint32_t* status) {
     using T = typename KT::T;
+    constexpr int SNT = SegScatterCfg<HV>::NT, SWARPS = SegScatterCfg<HV>::WARPS, SUB = SegScatterCfg<HV>::SUB;
     extern __shared__ __align__(16) char smem[];
     char* q = smem;
-    T* sk = reinterpret_cast<T*>(q);                     q += sizeof(T) * SEG_SUB;
-    uint32_t* sv = reinterpret_cast<uint32_t*>(q);       q += HV ? sizeof(uint32_t) * SEG_SUB : 0;
+    T* sk = reinterpret_cast<T*>(q);                     q += sizeof(T) * SUB;
+    uint32_t* sv = reinterpret_cast<uint32_t*>(q);       q += HV ? sizeof(uint32_t) * SUB : 0;
     uint32_t* tile_off = reinterpret_cast<uint32_t*>(q); q += sizeof(uint32_t) * (maxp + 1);
     uint32_t* cursor = reinterpret_cast<uint32_t*>(q);   q += sizeof(uint32_t) * maxp;
     uint32_t* scratch = reinterpret_cast<uint32_t*>(q);  q += sizeof(uint32_t) * 32;
-    uint16_t* sb = reinterpret_cast<uint16_t*>(q);       q += sizeof(uint16_t) * SEG_SUB;
-    uint16_t* cnt = reinterpret_cast<uint16_t*>(q);      // HV: [SEG_WARPS][p + 1]
+    uint16_t* sb = reinterpret_cast<uint16_t*>(q);       q += sizeof(uint16_t) * SUB;
+    uint16_t* cnt = reinterpret_cast<uint16_t*>(q);      // HV: [SWARPS][p + 1]
 
     const uint32_t T_ = tot->tiles;
     const uint32_t t0 = tile_lo(blockIdx.x, gridDim.x, T_), t1 = tile_lo(blockIdx.x + 1, gridDim.x, T_);
@@ -437,23 +447,24 @@ k_seg_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restric
         const uint32_t tl = t - seg_t0;
         const uint32_t seg_end = r.beg + r.len;
         __syncthreads();                                  // previous tile's cursors are no longer read
-        for (int b = threadIdx.x; b < p; b += SEG_NT) cursor[b] = r.beg + col[r.hist0 + (size_t)b * r.ntile + tl];
-        for (uint32_t sub = 0; sub < r.tile; sub += SEG_SUB) {
+        for (int b = threadIdx.x; b < p; b += SNT) cursor[b] = r.beg + col[r.hist0 + (size_t)b * r.ntile + tl];
+        const uint32_t tend = min(r.len, (tl + 1) * r.tile);   // end of this tile inside the segment
+        for (uint32_t sub = 0; sub < r.tile; sub += SUB) {
             const uint32_t lbase = tl * r.tile + sub;
-            if (lbase >= r.len) break;
+            if (lbase >= tend) break;
             const uint32_t base = lbase + w * (SEG_IT * 32) + lane;
             T kv[SEG_IT];
             uint32_t br[SEG_IT];   // bucket << 16 | rank inside the sub-tile's part of the bucket
 #pragma unroll
             for (int i = 0; i < SEG_IT; ++i) {
                 const uint32_t e = base + i * 32;
-                kv[i] = e < r.len ? keys[r.beg + e] : T(0);
-                br[i] = e < r.len ? (uint32_t)bid[r.beg + e] : (uint32_t)p;
+                kv[i] = e < tend ? keys[r.beg + e] : T(0);
+                br[i] = e < tend ? (uint32_t)bid[r.beg + e] : (uint32_t)p;
             }
             if (HV) {
                 for (int b = lane; b <= p; b += 32) mycnt[b] = 0;
             } else {
-                for (int b = threadIdx.x; b <= p; b += SEG_NT) tile_off[b] = 0;
+                for (int b = threadIdx.x; b <= p; b += SNT) tile_off[b] = 0;
             }
             __syncthreads();
             if (HV) {
@@ -469,10 +480,10 @@ k_seg_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restric
                     __syncwarp();
                 }
                 __syncthreads();
-                for (int b = threadIdx.x; b < p; b += SEG_NT) {
+                for (int b = threadIdx.x; b < p; b += SNT) {
                     uint32_t run = 0;
 #pragma unroll
-                    for (int ww = 0; ww < SEG_WARPS; ++ww) {
+                    for (int ww = 0; ww < SWARPS; ++ww) {
                         const uint32_t c = cnt[ww * cstride + b];
                         cnt[ww * cstride + b] = (uint16_t)run;
                         run += c;
@@ -493,7 +504,7 @@ k_seg_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restric
                 const int b = (int)(br[i] >> 16);
                 if (b < p) {
                     const uint32_t loc = tile_off[b] + (HV ? mycnt[b] : 0u) + (br[i] & 0xFFFFu);
-                    if (loc >= (uint32_t)SEG_SUB) {
+                    if (loc >= (uint32_t)SUB) {
                         flag_bounds(status, 10, loc);
                         continue;
                     }
@@ -503,7 +514,7 @@ k_seg_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restric
                 }
             }
             __syncthreads();
-            for (uint32_t j = threadIdx.x; j < tvalid; j += SEG_NT) {
+            for (uint32_t j = threadIdx.x; j < tvalid; j += SNT) {
                 const int b = sb[j];
                 const uint32_t dst = cursor[b] + (j - tile_off[b]);
                 if (dst < r.beg || dst >= seg_end) {
@@ -514,7 +525,7 @@ k_seg_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restric
                 if (HV) vout[dst] = sv[j];
             }
             __syncthreads();
-            for (int b = threadIdx.x; b < p; b += SEG_NT) cursor[b] += tile_off[b + 1] - tile_off[b];
+            for (int b = threadIdx.x; b < p; b += SNT) cursor[b] += tile_off[b + 1] - tile_off[b];
             __syncthreads();
         }
     }
