@@ -77,14 +77,14 @@ constexpr int TOP_IT = 16;           // keys per thread per tile
 constexpr int TOP_TILE = TOP_NT * TOP_IT;
 constexpr int TOP_WARPS = TOP_NT / 32;
 constexpr int TOP_SUPER = 2 * TOP_TILE;           // 8192 keys: the unit both top-level passes walk
-// Top-level classify and scatter: 4-byte keys alone are staged a whole unit at
-// a time by 512 threads (runs of twice as many keys per bucket); 8-byte keys
-// (already 32 bytes for 4 keys) and payload sorts (whose per-warp
-// stable-ranking counters must fit shared memory for p up to MAX_P) use 256
-// threads and two halves.  Classify uses the same thread count, since both
-// passes split the array among the same number of CTAs.
+// Top-level classify and scatter: keys alone are staged a whole unit at a time
+// by 512 threads (runs of twice as many keys per bucket, fewer partly written
+// 32-byte sectors); payload sorts (whose per-warp stable-ranking counters must
+// fit shared memory for p up to MAX_P) use 256 threads and two halves.
+// Classify uses the same thread count, since both passes split the array among
+// the same number of CTAs.
 template <class T, bool HV> struct ScatterCfg {
-    static constexpr int NT = (!HV && sizeof(T) == 4) ? 2 * TOP_NT : TOP_NT;
+    static constexpr int NT = !HV ? 2 * TOP_NT : TOP_NT;
     static constexpr int WARPS = NT / 32;
     static constexpr int SUB = NT * TOP_IT;
 };
