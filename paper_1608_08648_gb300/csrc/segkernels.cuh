@@ -299,21 +299,23 @@ k_seg_classify(const typename KT::T* __restrict__ keys, const SegRec* __restrict
         const uint32_t tl = t - seg_t0;
         for (int b = threadIdx.x; b <= p; b += SEG_NT) cnt[b] = 0;
         __syncthreads();
-        for (uint32_t sub = 0; sub < r.tile; sub += SEG_SUB) {
+        constexpr int CIT = SEG_IT;                        // (16 a thread measured slower: registers)
+        const uint32_t tend = min(r.len, (tl + 1) * r.tile);
+        for (uint32_t sub = 0; sub < r.tile; sub += SEG_NT * CIT) {
             const uint32_t lbase = tl * r.tile + sub;
-            if (lbase >= r.len) break;
-            const uint32_t base = lbase + w * (SEG_IT * 32) + lane;
-            O o[SEG_IT];
+            if (lbase >= tend) break;
+            const uint32_t base = lbase + w * (CIT * 32) + lane;
+            O o[CIT];
 #pragma unroll
-            for (int i = 0; i < SEG_IT; ++i) {
+            for (int i = 0; i < CIT; ++i) {
                 const uint32_t e = base + i * 32;
-                o[i] = e < r.len ? KT::ord(keys[r.beg + e]) : O(0);
+                o[i] = e < tend ? KT::ord(keys[r.beg + e]) : O(0);
             }
 #pragma unroll
-            for (int i = 0; i < SEG_IT; ++i) {
+            for (int i = 0; i < CIT; ++i) {
                 const uint32_t e = base + i * 32;
                 int b = p;                                  // past the end: a spare counter
-                if (e < r.len) {
+                if (e < tend) {
                     b = split_find<O>(tb, o[i], e);
                     bid[r.beg + e] = (uint16_t)b;
                 }
