@@ -187,20 +187,40 @@ def measured_traffic(kernel: str, dtype: str, n: int):
     return int(t["dram_bytes_per_key"][kernel] * n)
 
 
-def algorithmic_bytes(name: str, n: int, kb: int, vb: int, repart_keys: int) -> int:
-    """Bytes a kernel must move for one step (one full sort of n keys):
-    classify reads every key; scatter reads and writes every key (and payload);
-    a repartition level reads a key twice (count, scatter) and writes it once;
-    the leaf sort reads and writes every key once."""
+def algorithmic_bytes(name: str, n: int, kb: int, vb: int, repart_keys: int, split_keys: int = 0) -> int:
+    """Bytes a kernel must move for one step (one full sort of n keys), the minimum
+    ledger of one distribution level (no stored bucket ids): classify reads every key;
+    scatter reads and writes every key (and payload); the bucket phase's split does
+    the same for the keys of oversized buckets; a repartition level reads a key twice
+    (count, scatter) and writes it once; the leaf sort reads and writes every key."""
     if name == "k_classify":
         return n * kb
     if name == "k_scatter":
         return 2 * n * (kb + vb)
+    if name == "k_seg_classify":
+        return split_keys * kb
+    if name == "k_seg_scatter":
+        return 2 * split_keys * (kb + vb)
     if name == "k_leaf":
         return 2 * n * (kb + vb)
     if name == "k_repart":
-        return repart_keys * (2 * kb + vb) + repart_keys * (kb + vb)
+        rk = repart_keys - split_keys
+        return rk * (2 * kb + vb) + rk * (kb + vb)
     return 0
+
+
+def pipeline_ledger(n, kb, vb, split_keys, repart_keys, ms, peak):
+    """Whole-sort bytes: the passes this sort makes (with its 2-byte bucket ids) and the
+    minimum ledger of one distribution level (classify k, scatter 2k, sort 2k per key),
+    each against the step time."""
+    rk = repart_keys - split_keys
+    actual = (n * (kb + 2) + n * (2 * (kb + vb) + 2) + split_keys * (kb + 2) + split_keys * (2 * (kb + vb) + 2)
+              + rk * (3 * kb + 2 * vb) + 2 * n * (kb + vb))
+    minimum = n * (kb + 2 * (kb + vb) + 2 * (kb + vb))
+    t = ms / 1e3
+    return {"actual_bytes": actual, "actual_gbs": round(actual / t / 1e9, 1), "actual_frac": round(actual / t / 1e9 / peak, 4),
+            "min_bytes": minimum, "min_gbs": round(minimum / t / 1e9, 1), "min_frac": round(minimum / t / 1e9 / peak, 4),
+            "passes": "classify, scatter, bucket-phase split (classify + scatter), repartition, leaf sort"}
 
 
 # ---- batched segmented workload ------------------------------------------------------
@@ -377,7 +397,7 @@ def run_batched(a, rank, world, local, steps, warmup, plain_steps):
             n_part += x
     peaks, peak_kind = measured_peaks()
     dom = max(prof, key=lambda k: k["total_ms"])
-    alg = seg_alg_bytes(dom["name"], n, n_part, kb, ctr["repart_keys"])
+    alg = seg_alg_bytes(dom["name"], n, n_part, kb, ctr["repart_keys"] - ctr["split_keys"])
     achieved = alg / (dom["total_ms"] / 1e3) / 1e9 if dom["total_ms"] > 0 else 0.0
     roof = {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1), "peak": float(peaks["hbm_gbs"]),
             "unit": "GB/s", "frac": round(achieved / float(peaks["hbm_gbs"]), 4), "traffic": None,
@@ -753,6 +773,8 @@ def run_ours(a, rank, world, local):
     _, _, st = oss.sort(keys, split=a.split, p=a.p, s=a.s, seed=a.seed, out=out, workspace=ws, key_type=a.dtype,
                         stats=True)
     torch.cuda.synchronize()
+    _, ctr = oss.os_read_counters(ws.data_ptr(), sh)
+    split_keys = ctr["split_keys"]
 
     clocks = Clocks(local)
     barrier(world)
@@ -821,7 +843,7 @@ def run_ours(a, rank, world, local):
     dom = max(top, key=lambda k: k["total_ms"]) if top else None
     roof = None
     if dom:
-        alg = algorithmic_bytes(dom["name"], n, kb, vb, st["repart_keys"]) * a.steps
+        alg = algorithmic_bytes(dom["name"], n, kb, vb, st["repart_keys"], split_keys) * a.steps
         achieved = alg / (dom["total_ms"] / 1e3) / 1e9 if dom["total_ms"] > 0 else 0.0
         peak = float(peaks["hbm_gbs"])
         roof = {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1), "peak": peak,
@@ -829,7 +851,8 @@ def run_ours(a, rank, world, local):
                 "traffic": measured_traffic(dom["name"], a.dtype, n),
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "avg_launch_ms": round(dom["total_ms"] / dom["launches"], 4),
-                "alg_bytes_per_step": algorithmic_bytes(dom["name"], n, kb, vb, st["repart_keys"])}
+                "alg_bytes_per_step": algorithmic_bytes(dom["name"], n, kb, vb, st["repart_keys"], split_keys),
+                "pipeline": pipeline_ledger(n, kb, vb, split_keys, st["repart_keys"], ms, peak)}
 
     res = {"metric": "keys/s", "value": value, "unit": "keys/s", "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -842,7 +865,8 @@ def run_ours(a, rank, world, local):
            "kernels": [{"name": k["name"], "launches": k["launches"], "total_ms": round(k["total_ms"], 4),
                         "share": round(k["total_ms"] / max(1e-9, sum(x["total_ms"] for x in prof)), 4)}
                        for k in sorted(prof, key=lambda k: -k["total_ms"])],
-           "stats": {"max_bucket": st["max_bucket"], "depth": st["depth"], "repart_keys": st["repart_keys"]},
+           "stats": {"max_bucket": st["max_bucket"], "depth": st["depth"], "repart_keys": st["repart_keys"],
+                     "split_keys": split_keys},
            "context": {"torch_sort_ms": round(torch_sort_ms, 3),
                        "note": "torch.sort of the same keys (radix sort returning values and indices), not a baseline"}}
     if rank == 0 and world == 1 and not a.no_cpu:

@@ -438,6 +438,8 @@ int os_check(const void* d_ws, void* stream, uint32_t* bits);
  *   depth       : deepest in-bucket repartition level used.
  *   repart_keys : keys moved by in-bucket repartitions, summed over levels.
  *   bad_site, bad_index : first failed range check (0 when none).
+ *   split_keys  : the part of repart_keys moved by the first in-bucket level
+ *                 (the SqRan split of every oversized bucket).
  */
 typedef struct {
     uint32_t errors;
@@ -445,6 +447,7 @@ typedef struct {
     uint64_t repart_keys;
     uint32_t bad_site;
     uint32_t bad_index;
+    uint64_t split_keys;
 } os_counters;
 
 int os_read_counters(const void* d_ws, void* stream, os_counters* counters);

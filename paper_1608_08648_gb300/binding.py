@@ -37,7 +37,7 @@ class os_stats(ctypes.Structure):
 
 class os_counters(ctypes.Structure):
     _fields_ = [("errors", _u32), ("depth", _u32), ("repart_keys", _u64), ("bad_site", _u32),
-                ("bad_index", _u32)]
+                ("bad_index", _u32), ("split_keys", _u64)]
 
 
 class os_kernel_time(ctypes.Structure):
@@ -212,7 +212,7 @@ def os_read_counters(d_ws: int, stream: int | None) -> tuple[int, dict]:
     c = os_counters()
     rc = lib().os_read_counters(d_ws, stream, ctypes.byref(c))
     return rc, {"errors": int(c.errors), "depth": int(c.depth), "repart_keys": int(c.repart_keys),
-                "bad_site": int(c.bad_site), "bad_index": int(c.bad_index)}
+                "bad_site": int(c.bad_site), "bad_index": int(c.bad_index), "split_keys": int(c.split_keys)}
 
 
 def os_launch_count() -> int:

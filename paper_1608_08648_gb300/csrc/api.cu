@@ -144,7 +144,8 @@ int fill_stats(int kt, const RunArgs& a, cudaStream_t st, os_stats* stats) {
     const uint32_t p = a.prm.p, pu = a.res.p_used;
     stats->p_used = pu;
     stats->depth = status[1];
-    stats->repart_keys = (uint64_t)status[4] | ((uint64_t)status[5] << 32);
+    stats->repart_keys = ((uint64_t)status[2] | ((uint64_t)status[3] << 32)) +
+                         ((uint64_t)status[4] | ((uint64_t)status[5] << 32));
     if (pu == 1) {
         stats->max_bucket = a.n;
         if (stats->bucket_sizes) {
@@ -360,7 +361,8 @@ int os_read_counters(const void* d_ws, void* stream, os_counters* counters) {
     if (e != cudaSuccess) return cuda_fail(e);
     counters->errors = w[0];
     counters->depth = w[1];
-    counters->repart_keys = (uint64_t)w[4] | ((uint64_t)w[5] << 32);
+    counters->split_keys = (uint64_t)w[2] | ((uint64_t)w[3] << 32);
+    counters->repart_keys = counters->split_keys + ((uint64_t)w[4] | ((uint64_t)w[5] << 32));
     counters->bad_site = w[6];
     counters->bad_index = w[7];
     return OS_OK;

@@ -24,7 +24,8 @@ struct Ctx {
     cudaStream_t st = nullptr;
     Arena ar;
     int num_sms = 152;
-    uint32_t* status = nullptr;   // [0] error bits, [1] depth, [4..5] u64 repartitioned keys, [6..7] range check
+    uint32_t* status = nullptr;   // [0] error bits, [1] depth, [2..3] u64 keys split by the bucket phase's SqRan,
+                                  // [4..5] u64 keys repartitioned by k_repart, [6..7] range check
     bool nested = false;          // inside the sort of a sample (launch names get a ".sample" suffix)
     bool live() const { return !ar.measure() && !ar.failed; }
 };
@@ -173,7 +174,7 @@ void seg_core(Ctx& c, const SegSource& src, const SegClasses& cls, const typenam
                                                          (uint32_t)(static_cast<const void*>(alt) ==
                                                                     static_cast<const void*>(kin)),
                                                          c.status, c.status + 1,
-                                                         reinterpret_cast<unsigned long long*>(c.status + 4)));
+                                                         reinterpret_cast<unsigned long long*>(c.status + 2)));
     if (B.any_part) {
         const size_t sm_s = seg_scatter_smem<KT, HV>(B.maxp);
         cudaFuncSetAttribute(k_seg_scatter<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_s);
