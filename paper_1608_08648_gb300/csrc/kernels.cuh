@@ -1,13 +1,16 @@
 // Kernels of the GB300 oversampling sample sort.
 //
-// Paper step -> kernel:
-//   step 1 (SqDet BaselineSorting)      k_repart + k_leaf over p uniform sequences
+// Paper step -> kernel (the k_seg_* kernels are in segkernels.cuh):
+//   step 1 (SqDet BaselineSorting)      the segmented sort over p uniform sequences
 //   step 2 (SqDet regular sample)       k_det_sample
 //   step 2 (SqRan random sample)        k_ran_positions + k_gather_tagged
 //   steps 2-3 (sample sort, splitters)  k_leaf (or a nested sort) + k_pick_splitters
 //   step 4 (split)                      k_classify + k_column_scan + k_bucket_offsets
 //                                       + k_scatter (keys land in contiguous buckets)
-//   step 5 (sort every bucket)          k_repart + k_leaf over the p buckets
+//   step 5 (sort every bucket)          the segmented sort over the p buckets: an
+//                                       oversized bucket is split again by SqRan
+//                                       (k_seg_*), a rare oversized child by
+//                                       k_repart, every leaf by k_leaf
 #pragma once
 
 #include "blocksort.cuh"
@@ -327,16 +330,16 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Step 5 (and step 1 of SqDet): sort every segment of an array.
-// A segment of at most CAP keys is sorted in shared memory by one CTA
-// (k_leaf, block_merge_sort).  A larger one is repartitioned by one CTA
-// (k_repart) -- the introduction of the paper lets split keys be sorted again
-// with the same partitioning scheme: a stratified random sample of SAMPLE2 tagged keys gives
-// p2 - 1 splitters (tag = position inside the segment), a counting pass and a
-// stable scatter move the keys into p2 child segments in another buffer, and
-// the children go to the leaf list or to the next level's list.
-// Buffers: id 0 = src (level-0 data, never written), 1 = other, 2 = alt.
-// Children of a level-d repartition are written to `other` (d even) or `alt`
+// Step 5 (and step 1 of SqDet), after the segmented split: every leaf of at
+// most CAP keys is sorted in shared memory by one CTA (k_leaf).  A child still
+// larger than CAP is repartitioned by one CTA (k_repart) -- the introduction of
+// the paper lets split keys be sorted again with the same partitioning scheme:
+// a stratified random sample of SAMPLE2 tagged keys gives p2 - 1 splitters
+// (tag = position inside the segment), a counting pass and a stable scatter
+// move the keys into p2 child segments in another buffer, and the children go
+// to the leaf list or to the next level's list.
+// Buffers: id 0 = the segmented sort's input, 1 = its output, 2 = scratch.
+// Children of a level-d repartition are written to buffer 1 (d even) or 2
 // (d odd); leaves always write the sorted keys to `out`.
 // ---------------------------------------------------------------------------
 struct SegSpec {
@@ -621,8 +624,8 @@ __device__ __forceinline__ void push_item(WorkItem* list, uint32_t* count, uint3
     else atomicOr(status, ERR_SIZES);
 }
 
-// One repartition level.  Level 0 walks the segments of ss; level d >= 1 walks
-// the list filled by level d - 1.  Persistent: CTAs stride over the work.
+// One repartition level d >= 1: walks the list filled by level d - 1 (level 1:
+// by the segmented split).  Persistent: CTAs stride over the work.
 template <class KT, bool HV>
 __global__ void __launch_bounds__(BK_NT, 2)
 k_repart(int level, SegSpec ss, SortBufs<KT> bufs, WorkLists wl, uint64_t seed, uint32_t* status,
@@ -631,21 +634,14 @@ k_repart(int level, SegSpec ss, SortBufs<KT> bufs, WorkLists wl, uint64_t seed, 
     using L = BucketSmem<KT, HV>;
     extern __shared__ __align__(16) char smem[];
     uint32_t* off = reinterpret_cast<uint32_t*>(smem + L::bytes - sizeof(uint32_t) * (MAXP2 + 1) - 16);
-    const uint32_t nwork = level == 0 ? ss.nseg : min(wl.counts[level], wl.part_cap);
+    if (level < 1) return;
+    const uint32_t nwork = min(wl.counts[level], wl.part_cap);
     const WorkItem* in_list = wl.part[(level - 1) & 1];
     WorkItem* next_list = wl.part[level & 1];
     const uint32_t outbuf = (level & 1) ? 2u : 1u;
     for (uint32_t it = blockIdx.x; it < nwork; it += gridDim.x) {
-        uint32_t beg, len, inbuf;
-        if (level == 0) {
-            seg_bounds(ss, it, beg, len);
-            inbuf = 0;
-        } else {
-            const WorkItem w = in_list[it];
-            beg = w.beg;
-            len = w.len;
-            inbuf = w.buf;
-        }
+        const WorkItem w = in_list[it];
+        const uint32_t beg = w.beg, len = w.len, inbuf = w.buf;
         if (len == 0) continue;
         if (len <= (uint32_t)L::CAP) {
             if (threadIdx.x == 0) push_item(wl.leaf, &wl.counts[0], wl.leaf_cap, beg, len, inbuf, status);
