@@ -45,6 +45,8 @@ def parse():
                     help="buckets (default: 512 for int32 keys, 1024 for 8-byte keys; the fastest on GB300)")
     ap.add_argument("--s", type=int, default=16)
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--det-merge", action="store_true",
+                    help="SqDet with steps 4-5 as in Algorithm 1 (split the sorted sequences, merge every bucket)")
     ap.add_argument("--cpu-sample", type=int, default=1 << 25, help="keys of the oracle's timed sample")
     ap.add_argument("--ref-sample", type=int, default=1 << 20, help="keys per step of --impl reference")
     ap.add_argument("--no-e2e", action="store_true")
@@ -67,8 +69,9 @@ def parse():
 
 
 def workload_name(a, n):
+    org = ", steps 4-5 as split + merge" if a.det_merge else ""
     return (f"n={n} ({'2^%d' % (n.bit_length() - 1) if n & (n - 1) == 0 else n}) {a.dtype} {a.dist} "
-            f"seed {a.seed}, Sq{'Ran' if a.split == 'ran' else 'Det'} p={a.p} s={a.s}")
+            f"seed {a.seed}, Sq{'Ran' if a.split == 'ran' else 'Det'} p={a.p} s={a.s}{org}")
 
 
 def measured_peaks():
@@ -743,7 +746,7 @@ def run_ours(a, rank, world, local):
     kb, vb = KEY_BYTES[a.dtype], 0
     keys = inputs.keys(a.dist, n, a.dtype, seed=a.seed + rank, p=a.p, device=dev)
     out = torch.empty_like(keys)
-    prm = oss.params(a.split, a.p, a.s, a.seed)
+    prm = oss.params(a.split, a.p, a.s, a.seed, oss.OS_STABLE | (2 if a.det_merge else 0))
     rc, need = oss.os_workspace_size(kt, n, False, prm)
     assert rc == 0, oss.os_strerror(rc)
     ws = torch.empty(need, dtype=torch.uint8, device=dev)
@@ -771,7 +774,7 @@ def run_ours(a, rank, world, local):
                        torch.sort(out.view(torch.int64) if a.dtype != "i32" else out).values), "not a permutation"
     # statistics of one untimed sort: repartitioned keys (for the byte ledger)
     _, _, st = oss.sort(keys, split=a.split, p=a.p, s=a.s, seed=a.seed, out=out, workspace=ws, key_type=a.dtype,
-                        stats=True)
+                        stats=True, det_merge=a.det_merge)
     torch.cuda.synchronize()
     _, ctr = oss.os_read_counters(ws.data_ptr(), sh)
     split_keys = ctr["split_keys"]
@@ -858,7 +861,7 @@ def run_ours(a, rank, world, local):
            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": a.dtype, "data": "synthetic",
            "config": {"workload": workload_name(a, n), "n": n, "key": a.dtype, "dist": a.dist, "split": a.split,
-                      "p": a.p, "s": a.s, "seed": a.seed, "payload": False,
+                      "p": a.p, "s": a.s, "seed": a.seed, "payload": False, "det_merge": a.det_merge,
                       "l2": "inputs larger than L2 (no flush needed)", "parallelism": "replicas"},
            "roofline": roof, "e2e": e2e, "gpu_launches": launches,
            "clocks": clk,

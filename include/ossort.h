@@ -67,6 +67,11 @@ typedef enum {
 
 /* Flags of os_params.flags. */
 #define OS_STABLE 1u         /* accepted for clarity: the sort is always stable */
+#define OS_DET_MERGE 2u      /* OS_DET only: steps 4-5 as in Algorithm 1 -- split every sorted
+                                sequence by a binary search of the splitters, then merge the p
+                                pieces of every bucket -- instead of classifying and scattering
+                                every key and sorting every bucket again.  Same output, same
+                                splitters and bucket sizes. */
 
 /*
  * Parameters of one sort (Algorithm 1 / Algorithm 2 call SqDet(X, n, p, SomeSort)).
@@ -81,7 +86,7 @@ typedef enum {
  *   seed  : OS_RAN only: sample position j is floor(u_j n / 2^64), u_j the j-th
  *           output of stream 1 of the counter-based SplitMix64 keyed by seed
  *           (sampling with replacement over the original positions).
- *   flags : 0 or OS_STABLE.
+ *   flags : 0, OS_STABLE, OS_DET_MERGE (with OS_DET), or their or.
  * When the input is too small to sample (OS_RAN: n < 2 p s, the condition
  * p s < n/2 of Claim 1; OS_DET: ceil(n/p) < r p; or p = 1) the whole input is
  * one bucket: the call still sorts, and the statistics report p_used = 1.

@@ -58,10 +58,11 @@ def workspace_bytes(n, key_type="i32", has_vals=False, split="ran", p=1024, s=16
 
 
 def sort(keys, values=None, *, split="ran", p=1024, s=16, seed=0, out=None, values_out=None, workspace=None,
-         stream=None, key_type=None, stats=False):
+         stream=None, key_type=None, stats=False, det_merge=False):
     """Sort a CUDA tensor of keys (1-D int32, float64 or 64-bit unsigned held in int64/uint64;
     or uint8 of shape (n, 32): 32-byte strings in memcmp order), optionally carrying an
-    int32/uint32 payload, stably.  Returns (keys_out, values_out, stats)."""
+    int32/uint32 payload, stably.  det_merge (SqDet only): steps 4-5 as in Algorithm 1 (split the
+    sorted sequences, merge every bucket's pieces).  Returns (keys_out, values_out, stats)."""
     import torch
     assert keys.is_cuda and keys.is_contiguous()
     kt = _key_type(keys, key_type)
@@ -71,7 +72,7 @@ def sort(keys, values=None, *, split="ran", p=1024, s=16, seed=0, out=None, valu
     else:
         assert keys.dim() == 1
         n = keys.numel()
-    prm = params(split, p, s, seed)
+    prm = params(split, p, s, seed, OS_STABLE | (2 if det_merge else 0))
     hv = values is not None
     if out is None:
         out = torch.empty_like(keys)

@@ -15,6 +15,7 @@ OS_I32, OS_U64, OS_F64, OS_S32 = 0, 1, 2, 3
 OS_DET, OS_RAN = 0, 1
 OS_OK, OS_ERR_ARG, OS_ERR_WS, OS_ERR_UNSUPPORTED, OS_ERR_CUDA, OS_ERR_DEVICE = range(6)
 OS_STABLE = 1
+OS_DET_MERGE = 2
 OS_MAX_N = 1 << 31
 OS_MAX_P = 4096
 OS_MAX_PS = 1 << 24

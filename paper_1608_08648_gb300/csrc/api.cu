@@ -104,7 +104,8 @@ int check_params(int kt, uint64_t n, const os_params* prm) {
     if (kt < OS_I32 || kt > OS_S32 || !prm) return OS_ERR_ARG;
     if (prm->split != OS_DET && prm->split != OS_RAN) return OS_ERR_ARG;
     if (prm->p < 1 || prm->s < 1) return OS_ERR_ARG;
-    if (prm->flags & ~OS_STABLE) return OS_ERR_ARG;
+    if (prm->flags & ~(OS_STABLE | OS_DET_MERGE)) return OS_ERR_ARG;
+    if ((prm->flags & OS_DET_MERGE) && prm->split != OS_DET) return OS_ERR_ARG;
     if (n > OS_MAX_N || prm->p > OS_MAX_P || (uint64_t)prm->p * prm->s > OS_MAX_PS)
         return OS_ERR_UNSUPPORTED;
     return OS_OK;

@@ -400,6 +400,11 @@ struct TopResult {
 };
 
 template <class KT, bool HV>
+void det_merge_steps(Ctx& c, const typename KT::T* w1, const uint32_t* vw1, typename KT::T* w2, uint32_t* vw2,
+                     typename KT::T* kout, uint32_t* vout, uint32_t n, uint32_t p, const typename KT::O* spl_o,
+                     const uint32_t* spl_t, uint32_t* boff, uint32_t* bsize);
+
+template <class KT, bool HV>
 void sort_top(Ctx& c, const typename KT::T* kin, typename KT::T* kout, const uint32_t* vin, uint32_t* vout,
               uint32_t n, const os_params& prm, TopResult& res) {
     using T = typename KT::T;
@@ -435,8 +440,13 @@ void sort_top(Ctx& c, const typename KT::T* kin, typename KT::T* kout, const uin
         segment_sort<KT, HV>(c, SegSpec::even(p, n), kin, vin, w1, vw1, w2, vw2, internal_seed);
         res.det_index = vw1;
         splitters_det<KT>(c, w1, n, p, s, internal_seed, spl_o, spl_t);
-        partition_top<KT, HV>(c, w1, vw1, n, spl_o, spl_t, p, w2, vw2, boff, bsize);
-        segment_sort<KT, HV>(c, SegSpec::offsets(boff, p, n), w2, vw2, kout, vout, w2, vw2, internal_seed);
+        if (prm.flags & OS_DET_MERGE) {
+            // the paper's steps 4-5: split the sorted sequences, merge every bucket
+            det_merge_steps<KT, HV>(c, w1, vw1, w2, vw2, kout, vout, n, p, spl_o, spl_t, boff, bsize);
+        } else {
+            partition_top<KT, HV>(c, w1, vw1, n, spl_o, spl_t, p, w2, vw2, boff, bsize);
+            segment_sort<KT, HV>(c, SegSpec::offsets(boff, p, n), w2, vw2, kout, vout, w2, vw2, internal_seed);
+        }
     }
 }
 
@@ -484,3 +494,5 @@ int run_f64(RunArgs& a);
 int run_s32(RunArgs& a);
 
 }  // namespace ossort
+
+#include "detmerge.cuh"
