@@ -312,23 +312,35 @@ k_det_merge(int level, uint32_t p, uint64_t n, const typename KT::T* __restrict_
             if (sk[st + na + dd - 1 - mid] < sk[st + mid]) h2 = mid;
             else l2 = mid + 1;
         }
-        uint32_t ia = l2, ib = dd - l2;
+        // the two run heads stay in registers: one shared load per output
+        uint32_t ai = st + l2, ae = st + na, bi = st + na + (dd - l2), be = st + na + nb;
+        O ka = sk[min(ai, (uint32_t)DM_OT - 1)], kb = sk[min(bi, (uint32_t)DM_OT - 1)];
         cnt = (int)min((uint32_t)DM_IT, total - od);
 #pragma unroll
         for (int i = 0; i < DM_IT; ++i) {
             if (i < cnt) {
-                while (ia + ib == na + nb && sg + 1 < nseg) {   // this segment is done: the next one
-                    ++sg;
-                    seg(sg, st, na, nb);
-                    ia = 0;
-                    ib = 0;
+                if (ai == ae && bi == be && sg + 1 < nseg) {   // segment done: the next non-empty one
+                    do {
+                        ++sg;
+                        seg(sg, st, na, nb);
+                    } while (na + nb == 0 && sg + 1 < nseg);
+                    ai = st;
+                    ae = st + na;
+                    bi = ae;
+                    be = ae + nb;
+                    ka = sk[min(ai, (uint32_t)DM_OT - 1)];
+                    kb = sk[min(bi, (uint32_t)DM_OT - 1)];
                 }
-                const bool take_b = ia >= na || (ib < nb && sk[st + na + ib] < sk[st + ia]);
-                const uint32_t si = take_b ? st + na + ib : st + ia;
-                x[i] = sk[si];
-                if (HV) xv[i] = sv[si];
-                ia += take_b ? 0 : 1;
-                ib += take_b ? 1 : 0;
+                const bool take_b = ai == ae || (bi < be && kb < ka);
+                x[i] = take_b ? kb : ka;
+                if (HV) xv[i] = sv[take_b ? bi : ai];
+                if (take_b) {
+                    ++bi;
+                    kb = sk[min(bi, (uint32_t)DM_OT - 1)];
+                } else {
+                    ++ai;
+                    ka = sk[min(ai, (uint32_t)DM_OT - 1)];
+                }
             }
         }
     }
