@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--det-merge", action="store_true",
                     help="SqDet with steps 4-5 as in Algorithm 1 (split the sorted sequences, merge every bucket)")
-    ap.add_argument("--cpu-sample", type=int, default=1 << 25, help="keys of the oracle's timed sample")
+    ap.add_argument("--cpu-sample", type=int, default=1 << 24, help="keys of the oracle's timed sample")
     ap.add_argument("--ref-sample", type=int, default=1 << 20, help="keys per step of --impl reference")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -925,9 +925,30 @@ def cpu_cores():
         return os.cpu_count()
 
 
+def cpu_model():
+    """The host CPU's model name (x86: /proc/cpuinfo; Arm: lscpu), else the machine type."""
+    import platform
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
 def cpu_baseline(a):
-    """The oracle as it stands, single-threaded, on the first cpu_sample keys of the same
-    seeded workload."""
+    """The oracle as it stands on the first cpu_sample keys of the same seeded
+    workload, median of three runs, single-threaded (the reported baseline); beside
+    it, on the same keys, the oracle's multi-core form (Section 2.4: steps 1 and 5
+    over every host core) and SomeSort alone (the paper's stand-alone column)."""
     import numpy as np
 
     import oracle
@@ -936,11 +957,29 @@ def cpu_baseline(a):
     keys = inputs.keys(a.dist, a.keys, a.dtype, seed=a.seed, p=a.p, count=m).numpy()
     if a.dtype == "u64":
         keys = keys.view(np.uint64)
-    t0 = time.perf_counter()
-    oracle.sort(keys, a.dtype, a.split, a.p, a.s, seed=a.seed)
-    t = time.perf_counter() - t0
-    return {"value": m / t, "unit": "keys/s", "cores": 1, "kind": "oracle", "host_cores": cpu_cores(),
-            "sample": f"first {m} keys of the same seeded workload, one oracle run ({t:.2f} s)"}
+    cores = cpu_cores()
+
+    def med3(fn):
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        return statistics.median(ts)
+
+    t = med3(lambda: oracle.sort(keys, a.dtype, a.split, a.p, a.s, seed=a.seed))
+    t_mc = med3(lambda: oracle.sort(keys, a.dtype, a.split, a.p, a.s, seed=a.seed, threads=cores,
+                                    par_step5=True))
+    t_ss = med3(lambda: oracle.some_sort(keys, a.dtype))
+    return {"value": m / t, "unit": "keys/s", "cores": 1, "kind": "oracle", "host_cores": cores,
+            "cpu_model": cpu_model(),
+            "sample": f"first {m} keys of the same seeded workload, median of 3 oracle runs ({t:.2f} s)",
+            "multicore": {"value": m / t_mc, "unit": "keys/s", "cores": min(cores, a.p),
+                          "kind": "oracle, multi-core form (steps 1 and 5 over the host cores)",
+                          "seconds": round(t_mc, 3)},
+            "some_sort_alone": {"value": m / t_ss, "unit": "keys/s", "cores": 1,
+                                "kind": "oracle's SomeSort (stable merge sort) on the whole sample",
+                                "seconds": round(t_ss, 3)}}
 
 
 # ---- reference arm: the CPU oracle ------------------------------------------------

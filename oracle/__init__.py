@@ -34,7 +34,7 @@ def build(force: bool = False) -> str:
         os.path.getmtime(f) > os.path.getmtime(_LIB) for f in (_SRC, _HDR))
     if stale:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-std=gnu11", "-O2", "-fPIC", "-shared", "-Wall",
+        subprocess.check_call(["gcc", "-std=gnu11", "-O2", "-fPIC", "-shared", "-Wall", "-pthread",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -58,6 +58,11 @@ def _load():
         lib.oracle_sort.restype = i32
         lib.oracle_sort.argtypes = [i32, vp, vp, u64, i32, u32, u32, u64,
                                     vp, vp, vp, vp, vp, vp]
+        lib.oracle_sort_mc.restype = i32
+        lib.oracle_sort_mc.argtypes = [i32, vp, vp, u64, i32, u32, u32, u64,
+                                       vp, vp, vp, vp, vp, vp, u32, i32]
+        lib.oracle_some_sort.restype = i32
+        lib.oracle_some_sort.argtypes = [i32, vp, vp, u64, vp, vp]
         _lib = lib
     return _lib
 
@@ -88,12 +93,15 @@ def _ptr(a):
 
 
 def sort(keys: np.ndarray, kt: str, split: str, p: int, s: int, seed: int = 0,
-         vals: np.ndarray | None = None, merge: bool = True) -> dict:
+         vals: np.ndarray | None = None, merge: bool = True, threads: int = 1,
+         par_step5: bool = False) -> dict:
     """Run SqDet / SqRan on the CPU.
 
     Returns a dict with ``keys`` / ``vals`` (the output Y, when ``merge``),
     ``spl_keys`` and ``spl_tags`` (the p-1 tagged splitters), ``bucket_sizes``
-    (p entries) and ``p_used`` (p, or 1 when the input is too small to sample)."""
+    (p entries) and ``p_used`` (p, or 1 when the input is too small to sample).
+    ``threads`` > 1 runs the multi-core form of Section 2.4 (McDet / McRan: step 1
+    over that many threads, and step 5 too when ``par_step5``)."""
     lib = _load()
     keys = np.ascontiguousarray(keys, dtype=NP_DT[kt])
     if kt == "s32":
@@ -109,9 +117,12 @@ def sort(keys: np.ndarray, kt: str, split: str, p: int, s: int, seed: int = 0,
     spl_t = np.zeros(max(p - 1, 0), dtype=np.uint64)
     sizes = np.zeros(p, dtype=np.uint64)
     p_used = ctypes.c_uint32(0)
-    rc = lib.oracle_sort(KT[kt], _ptr(keys), _ptr(vals), n, SPLIT[split], p, s, seed,
-                         _ptr(out_k), _ptr(out_v), _ptr(spl_k), _ptr(spl_t), _ptr(sizes),
-                         ctypes.byref(p_used))
+    args = (KT[kt], _ptr(keys), _ptr(vals), n, SPLIT[split], p, s, seed,
+            _ptr(out_k), _ptr(out_v), _ptr(spl_k), _ptr(spl_t), _ptr(sizes), ctypes.byref(p_used))
+    if threads > 1:
+        rc = lib.oracle_sort_mc(*args, threads, 1 if par_step5 else 0)
+    else:
+        rc = lib.oracle_sort(*args)
     if rc != 0:
         raise RuntimeError(f"oracle_sort failed with code {rc}")
     pu = int(p_used.value)
@@ -120,3 +131,21 @@ def sort(keys: np.ndarray, kt: str, split: str, p: int, s: int, seed: int = 0,
         spl_t = spl_t[:0]
     return {"keys": out_k, "vals": out_v, "spl_keys": spl_k, "spl_tags": spl_t,
             "bucket_sizes": sizes, "p_used": pu}
+
+
+def some_sort(keys: np.ndarray, kt: str, vals: np.ndarray | None = None) -> dict:
+    """SomeSort (the oracle's stable merge sort) on the whole input: the
+    stand-alone sort the paper's tables compare against."""
+    lib = _load()
+    keys = np.ascontiguousarray(keys, dtype=NP_DT[kt])
+    if kt == "s32":
+        keys = keys.reshape(-1, 32)
+    n = keys.shape[0]
+    if vals is not None:
+        vals = np.ascontiguousarray(vals, dtype=np.uint32)
+    out_k = np.empty(keys.shape, dtype=NP_DT[kt])
+    out_v = np.empty(n, dtype=np.uint32) if vals is not None else None
+    rc = lib.oracle_some_sort(KT[kt], _ptr(keys), _ptr(vals), n, _ptr(out_k), _ptr(out_v))
+    if rc != 0:
+        raise RuntimeError(f"oracle_some_sort failed with code {rc}")
+    return {"keys": out_k, "vals": out_v}

@@ -33,6 +33,7 @@
 #include "oracle.h"
 
 #include <math.h>
+#include <pthread.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -204,13 +205,79 @@ static void write_outputs(int kt, const rec_t* y, uint64_t n, void* out_keys, ui
         for (uint64_t i = 0; i < n; ++i) out_vals[i] = y[i].val;
 }
 
-int oracle_sort(int kt, const void* keys, const uint32_t* vals, uint64_t n,
-                int split, uint32_t p, uint32_t s, uint64_t seed,
-                void* out_keys, uint32_t* out_vals,
-                void* spl_keys, uint64_t* spl_tags, uint64_t* bucket_sizes,
-                uint32_t* p_used) {
+/* ---- the multi-core adaptation (Section 2.4): whole steps split over threads -- */
+/* Worker w of t takes the sequences (step 1) or buckets (step 5) [w p / t, (w+1) p / t). */
+typedef struct {
+    int kt, rc;
+    uint32_t p, lo, hi;
+    rec_t* X;
+    const uint64_t* cs;
+    const uint64_t* pos;      /* step 5: split positions, p x (p + 1) */
+    const uint64_t* yoff;     /* step 5: first output position of every bucket */
+    rec_t* Y;
+} work_t;
+
+static void* step1_worker(void* arg) {
+    work_t* w = (work_t*)arg;
+    for (uint32_t k = w->lo; k < w->hi && !w->rc; ++k)
+        w->rc = some_sort(w->kt, w->X + w->cs[k], w->cs[k + 1] - w->cs[k]);
+    return NULL;
+}
+
+static void* step5_worker(void* arg) {
+    work_t* w = (work_t*)arg;
+    run_t* runs = (run_t*)malloc((size_t)w->p * sizeof(run_t));
+    if (!runs) { w->rc = -2; return NULL; }
+    for (uint32_t j = w->lo; j < w->hi && !w->rc; ++j) {
+        for (uint32_t k = 0; k < w->p; ++k) {
+            const uint64_t* pk = w->pos + (size_t)k * (w->p + 1);
+            runs[k].cur = w->X + w->cs[k] + pk[j];
+            runs[k].end = w->X + w->cs[k] + pk[j + 1];
+        }
+        w->rc = multiway_merge(w->kt, runs, w->p, w->Y + w->yoff[j]);
+    }
+    free(runs);
+    return NULL;
+}
+
+/* Run fn over t workers (t = 1: inline, no thread).  Returns the first error. */
+static int run_workers(void* (*fn)(void*), work_t* proto, uint32_t t) {
+    if (t <= 1) {
+        proto->lo = 0;
+        proto->hi = proto->p;
+        fn(proto);
+        return proto->rc;
+    }
+    work_t* ws = (work_t*)malloc((size_t)t * sizeof(work_t));
+    pthread_t* th = (pthread_t*)malloc((size_t)t * sizeof(pthread_t));
+    int rc = 0;
+    if (!ws || !th) { free(ws); free(th); return -2; }
+    uint32_t started = 0;
+    for (uint32_t w = 0; w < t; ++w) {
+        ws[w] = *proto;
+        ws[w].rc = 0;
+        ws[w].lo = (uint32_t)(((uint64_t)w * proto->p) / t);
+        ws[w].hi = (uint32_t)(((uint64_t)(w + 1) * proto->p) / t);
+        if (pthread_create(&th[w], NULL, fn, &ws[w]) != 0) { rc = -2; break; }
+        ++started;
+    }
+    for (uint32_t w = 0; w < started; ++w) {
+        pthread_join(th[w], NULL);
+        if (!rc) rc = ws[w].rc;
+    }
+    free(th);
+    free(ws);
+    return rc;
+}
+
+static int sort_impl(int kt, const void* keys, const uint32_t* vals, uint64_t n,
+                     int split, uint32_t p, uint32_t s, uint64_t seed,
+                     void* out_keys, uint32_t* out_vals,
+                     void* spl_keys, uint64_t* spl_tags, uint64_t* bucket_sizes,
+                     uint32_t* p_used, uint32_t threads, int par_step5) {
     if (kt < ORC_I32 || kt > ORC_S32 || (split != ORC_DET && split != ORC_RAN)) return -1;
     if (p < 1 || s < 1 || (n > 0 && !keys)) return -1;
+    const uint32_t t = threads < 1 ? 1 : (threads > p ? p : threads);
     g_str_keys = kt == ORC_S32 ? (const unsigned char*)keys : NULL;
 
     rec_t* X = (rec_t*)malloc((n ? n : 1) * sizeof(rec_t));
@@ -235,12 +302,14 @@ int oracle_sort(int kt, const void* keys, const uint32_t* vals, uint64_t n,
         return 0;
     }
 
-    /* Step 1, BaselineSorting: p sequences, each sorted by SomeSort. */
+    /* Step 1, BaselineSorting: p sequences, each sorted by SomeSort (over t
+     * threads in the multi-core form). */
     uint64_t* cs = (uint64_t*)malloc(((size_t)p + 1) * sizeof(uint64_t));
     if (!cs) { free(X); return -2; }
     for (uint64_t k = 0; k <= p; ++k) cs[k] = (uint64_t)(((unsigned __int128)k * n) / p);
-    for (uint32_t k = 0; k < p; ++k) {
-        int rc = some_sort(kt, X + cs[k], cs[k + 1] - cs[k]);
+    {
+        work_t w1 = {kt, 0, p, 0, p, X, cs, NULL, NULL, NULL};
+        int rc = run_workers(step1_worker, &w1, t);
         if (rc) { free(cs); free(X); return rc; }
     }
     if (split == ORC_DET)
@@ -314,30 +383,68 @@ int oracle_sort(int kt, const void* keys, const uint32_t* vals, uint64_t n,
     }
     if (p_used) *p_used = p;
 
-    /* Step 5: p-way merge of X_{0..p-1, j} into Y_j; Y is their concatenation. */
+    /* Step 5: p-way merge of X_{0..p-1, j} into Y_j; Y is their concatenation
+     * (bucket j starts after buckets 0..j-1).  The multi-core form may give
+     * every thread its own buckets. */
     if (out_keys) {
         rec_t* Y = (rec_t*)malloc((n ? n : 1) * sizeof(rec_t));
-        run_t* runs = (run_t*)malloc((size_t)p * sizeof(run_t));
-        if (!Y || !runs) rc = -2;
-        uint64_t o = 0;
-        for (uint32_t j = 0; !rc && j < p; ++j) {
-            uint64_t len = 0;
-            for (uint32_t k = 0; k < p; ++k) {
-                const uint64_t* pk = pos + (size_t)k * (p + 1);
-                runs[k].cur = X + cs[k] + pk[j];
-                runs[k].end = X + cs[k] + pk[j + 1];
-                len += pk[j + 1] - pk[j];
+        uint64_t* yoff = (uint64_t*)malloc(((size_t)p + 1) * sizeof(uint64_t));
+        if (!Y || !yoff) rc = -2;
+        if (!rc) {
+            yoff[0] = 0;
+            for (uint32_t j = 0; j < p; ++j) {
+                uint64_t len = 0;
+                for (uint32_t k = 0; k < p; ++k) {
+                    const uint64_t* pk = pos + (size_t)k * (p + 1);
+                    len += pk[j + 1] - pk[j];
+                }
+                yoff[j + 1] = yoff[j] + len;
             }
-            rc = multiway_merge(kt, runs, p, Y + o);
-            o += len;
+            work_t w5 = {kt, 0, p, 0, p, X, cs, pos, yoff, Y};
+            rc = run_workers(step5_worker, &w5, par_step5 ? t : 1);
         }
         if (!rc) write_outputs(kt, Y, n, out_keys, out_vals);
-        free(runs);
+        free(yoff);
         free(Y);
     }
     free(pos);
     free(S);
     free(cs);
+    free(X);
+    return rc;
+}
+
+int oracle_sort(int kt, const void* keys, const uint32_t* vals, uint64_t n,
+                int split, uint32_t p, uint32_t s, uint64_t seed,
+                void* out_keys, uint32_t* out_vals,
+                void* spl_keys, uint64_t* spl_tags, uint64_t* bucket_sizes,
+                uint32_t* p_used) {
+    return sort_impl(kt, keys, vals, n, split, p, s, seed, out_keys, out_vals, spl_keys, spl_tags,
+                     bucket_sizes, p_used, 1, 0);
+}
+
+int oracle_sort_mc(int kt, const void* keys, const uint32_t* vals, uint64_t n,
+                   int split, uint32_t p, uint32_t s, uint64_t seed,
+                   void* out_keys, uint32_t* out_vals,
+                   void* spl_keys, uint64_t* spl_tags, uint64_t* bucket_sizes,
+                   uint32_t* p_used, uint32_t threads, int par_step5) {
+    return sort_impl(kt, keys, vals, n, split, p, s, seed, out_keys, out_vals, spl_keys, spl_tags,
+                     bucket_sizes, p_used, threads, par_step5);
+}
+
+int oracle_some_sort(int kt, const void* keys, const uint32_t* vals, uint64_t n,
+                     void* out_keys, uint32_t* out_vals) {
+    if (kt < ORC_I32 || kt > ORC_S32 || (n > 0 && !keys)) return -1;
+    g_str_keys = kt == ORC_S32 ? (const unsigned char*)keys : NULL;
+    rec_t* X = (rec_t*)malloc((n ? n : 1) * sizeof(rec_t));
+    if (!X) return -2;
+    for (uint64_t i = 0; i < n; ++i) {
+        X[i].key = load_key(kt, keys, i);
+        X[i].tag = i;
+        X[i].val = vals ? vals[i] : 0u;
+    }
+    int rc = some_sort(kt, X, n);
+    if (!rc) write_outputs(kt, X, n, out_keys, out_vals);
     free(X);
     return rc;
 }

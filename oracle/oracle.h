@@ -68,6 +68,24 @@ int oracle_sort(int kt, const void* keys, const uint32_t* vals, uint64_t n,
                 void* spl_keys, uint64_t* spl_tags, uint64_t* bucket_sizes,
                 uint32_t* p_used);
 
+/*
+ * The multi-core adaptation of Section 2.4 (McDet / McRan): the same call with
+ * the p sorts of step 1 split over `threads` POSIX threads (worker w takes the
+ * sequences [w p / t, (w+1) p / t), t = min(threads, p)) and, when par_step5 is
+ * non-zero, the p merges of step 5 split the same way (the paper's measured
+ * McRan leaves step 5 sequential).  Same outputs as oracle_sort, bit for bit.
+ */
+int oracle_sort_mc(int kt, const void* keys, const uint32_t* vals, uint64_t n,
+                   int split, uint32_t p, uint32_t s, uint64_t seed,
+                   void* out_keys, uint32_t* out_vals,
+                   void* spl_keys, uint64_t* spl_tags, uint64_t* bucket_sizes,
+                   uint32_t* p_used, uint32_t threads, int par_step5);
+
+/* SomeSort alone on the whole input (the stable merge sort of step 1), the
+ * stand-alone column of the paper's tables: (key, original index) order. */
+int oracle_some_sort(int kt, const void* keys, const uint32_t* vals, uint64_t n,
+                     void* out_keys, uint32_t* out_vals);
+
 #ifdef __cplusplus
 }
 #endif
