@@ -212,17 +212,32 @@ def algorithmic_bytes(name: str, n: int, kb: int, vb: int, repart_keys: int, spl
     return 0
 
 
-def pipeline_ledger(n, kb, vb, split_keys, repart_keys, ms, peak):
+PIPELINE_KERNELS = ("k_classify", "k_scatter", "k_seg_classify", "k_seg_scatter", "k_leaf")
+
+
+def pipeline_ledger(n, kb, vb, split_keys, repart_keys, ms, peak, dtype=None, p=None):
     """Whole-sort bytes: the passes this sort makes (with its 2-byte bucket ids) and the
     minimum ledger of one distribution level (classify k, scatter 2k, sort 2k per key),
-    each against the step time."""
+    each against the step time; the DRAM bytes the committed ncu capture measured for
+    the same passes (per key, scaled to n; None once the kernels changed); and the
+    comparison work n (lg p + lg(n/p)) = n lg n as a secondary figure."""
     rk = repart_keys - split_keys
     actual = (n * (kb + 2) + n * (2 * (kb + vb) + 2) + split_keys * (kb + 2) + split_keys * (2 * (kb + vb) + 2)
               + rk * (3 * kb + 2 * vb) + 2 * n * (kb + vb))
     minimum = n * (kb + 2 * (kb + vb) + 2 * (kb + vb))
     t = ms / 1e3
+    ncu = None
+    if dtype is not None and vb == 0:
+        per = [measured_traffic(k, dtype, n) for k in PIPELINE_KERNELS]
+        if all(x is not None for x in per):
+            ncu = sum(per)
+    comps = n * math.log2(n) if n > 1 else 0.0
     return {"actual_bytes": actual, "actual_gbs": round(actual / t / 1e9, 1), "actual_frac": round(actual / t / 1e9 / peak, 4),
             "min_bytes": minimum, "min_gbs": round(minimum / t / 1e9, 1), "min_frac": round(minimum / t / 1e9 / peak, 4),
+            "ncu_dram_bytes": ncu,
+            "ncu_note": "DRAM read + write of the five passes from the committed ncu capture at 2^25 keys, "
+                        "scaled per key (part of that capture's traffic stays in the 129 MB L2)",
+            "comparisons": round(comps), "gcomparisons_per_s": round(comps / t / 1e9, 1),
             "passes": "classify, scatter, bucket-phase split (classify + scatter), repartition, leaf sort"}
 
 
@@ -855,7 +870,7 @@ def run_ours(a, rank, world, local):
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "avg_launch_ms": round(dom["total_ms"] / dom["launches"], 4),
                 "alg_bytes_per_step": algorithmic_bytes(dom["name"], n, kb, vb, st["repart_keys"], split_keys),
-                "pipeline": pipeline_ledger(n, kb, vb, split_keys, st["repart_keys"], ms, peak)}
+                "pipeline": pipeline_ledger(n, kb, vb, split_keys, st["repart_keys"], ms, peak, a.dtype, a.p)}
 
     res = {"metric": "keys/s", "value": value, "unit": "keys/s", "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
