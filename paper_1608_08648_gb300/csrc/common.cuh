@@ -99,11 +99,12 @@ constexpr int SAMPLE2 = 4096;        // sample size of an in-bucket repartition
 // Largest segment the shared-memory bucket sort takes: 8192 keys of 4 bytes,
 // 4096 of 8 bytes.
 template <class O> struct Cap { static constexpr int v = sizeof(O) == 4 ? 8192 : 4096; };
-// Threads and keys per thread of the leaf sort: keys alone use 256 threads with
-// 32 (4-byte) or 16 (8-byte) keys each; (key, position) pairs use 512 threads
-// with half as many, to stay within 64 registers.
+// Threads and keys per thread of the leaf sort: 4-byte keys alone use 128
+// threads with 64 keys each (one shared-memory merge round fewer; 80 registers,
+// six CTAs per SM), 8-byte keys alone 256 threads with 16; (key, position) pairs
+// use 512 threads with half the 256-thread count, to stay within 64 registers.
 template <class O, bool HV> struct LeafCfg {
-    static constexpr int NT = HV ? 512 : 256;
+    static constexpr int NT = HV ? 512 : (sizeof(O) == 4 ? 128 : 256);
     static constexpr int IT = Cap<O>::v / NT;
 };
 

@@ -671,8 +671,11 @@ k_repart(int level, SegSpec ss, SortBufs<KT> bufs, WorkLists wl, uint64_t seed, 
 
 // Shared-memory sort of every leaf: the segments of ss directly (direct = true)
 // or the leaf list.  Persistent: CTAs stride over the work.
-// Resident leaf CTAs per SM the register budget is sized for (64 registers).
-template <class KT, bool HV> struct LeafOcc { static constexpr int v = 65536 / (64 * LeafCfg<typename KT::O, HV>::NT); };
+// Resident leaf CTAs per SM the register budget is sized for: 64 registers a
+// thread, except 4-byte keys alone (six 128-thread CTAs, up to 85 registers).
+template <class KT, bool HV> struct LeafOcc {
+    static constexpr int v = (sizeof(typename KT::O) == 4 && !HV) ? 6 : 65536 / (64 * LeafCfg<typename KT::O, HV>::NT);
+};
 
 template <class KT, bool HV>
 __global__ void __launch_bounds__(LeafCfg<typename KT::O, HV>::NT, LeafOcc<KT, HV>::v)
