@@ -322,7 +322,7 @@ int os_seg_default_classes(int key_type, uint64_t max_len, os_seg_class* classes
  * class table (the whole-segment cutoff, and p, s and tile per length class)
  * by coordinate descent from os_seg_default_classes: cutoff in {capacity/2,
  * capacity, 2 capacity}; per class (largest share of keys first)
- * p in {p/4, p/2, 2p, 4p}, s in {4, 8, 16, 32, 64}, tile in {2048, 4096, 8192},
+ * p in {p/4, p/2, 2p, 4p}, s in {4, 8, 16, 32, 64}, tile in {2048, 4096, 8192, 16384},
  * keeping a change only when it lowers the median of `reps` timed runs.
  *   h_seg_offsets : the same offsets as d_seg_offsets, in HOST memory.
  *   d_keys_out, d_vals_out : scratch the trial sorts write.

@@ -21,7 +21,7 @@ struct os_graph_s {
 namespace {
 
 constexpr uint32_t TUNE_S[] = {4, 8, 16, 32, 64};
-constexpr uint32_t TUNE_TILE[] = {2048, 4096, 8192};
+constexpr uint32_t TUNE_TILE[] = {2048, 4096, 8192, 16384};
 constexpr uint32_t TUNE_MAX_P = OS_SEG_MAX_PS / 4;   // p s <= OS_SEG_MAX_PS with s >= 4
 
 uint64_t leaf_cap(int kt) { return kt == OS_I32 ? 8192 : 4096; }

@@ -106,7 +106,7 @@ SegClasses bucket_classes() {
     constexpr uint32_t CAP = (uint32_t)Cap<O>::v;
     SegClasses t{};
     t.n = 1;
-    t.c[0] = SegClass{CAP, 1u, 1u, 4096u, 0u};
+    t.c[0] = SegClass{CAP, 1u, 1u, 16384u, 0u};   // histogram tiles of the split (measured best of 4K..64K)
     t.auto_child = (CAP * 18u) / 25u;
     t.auto_pmax = 1024;                 // s >= 4 with p s <= SEG_SAMPLE
     t.auto_s = 64;

@@ -155,7 +155,7 @@ def test_tuner_returns_a_valid_table_that_sorts():
     assert ms > 0 and len(classes) >= 2 and classes[0][1] == 1
     assert [c[0] for c in classes] == sorted(set(c[0] for c in classes))
     for _, p, s, tile in classes[1:]:
-        assert 2 <= p <= 1024 and p * s <= B.OS_SEG_MAX_PS and tile in (2048, 4096, 8192)
+        assert 2 <= p <= 1024 and p * s <= B.OS_SEG_MAX_PS and tile in (2048, 4096, 8192, 16384)
     out, _, st = oss.sort_segmented(keys, off.cuda(), classes=classes, seed=5, key_type=kt, stats=True)
     torch.cuda.synchronize()
     check_against_oracle(kt, classes, 5, off, keys, None, out, None, st, segs=range(0, 300, 7))
