@@ -281,7 +281,8 @@ void partition_top(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, uint
                    const typename KT::O* spl_o, const uint32_t* spl_t, uint32_t p, typename KT::T* dst,
                    uint32_t* vdst, uint32_t* boff, uint32_t* bsize) {
     const int lb = table_lbits(p);
-    const uint32_t ntiles = (n + TOP_SUPER - 1) / TOP_SUPER;
+    constexpr uint32_t SUPER = ScatterCfg<typename KT::T, HV>::SUPER;
+    const uint32_t ntiles = (n + SUPER - 1) / SUPER;
     const uint32_t gmax = std::min<uint32_t>(std::max<uint32_t>(ntiles, 1), G_CAP);
     uint32_t* hist = c.ar.take<uint32_t>((size_t)p * gmax);
     uint32_t* col = c.ar.take<uint32_t>((size_t)p * gmax);
@@ -289,12 +290,12 @@ void partition_top(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, uint
     if (!c.live()) return;
     constexpr int NTS = ScatterCfg<typename KT::T, HV>::NT;
     const size_t sm_c = classify_smem<KT>(p, lb), sm_s = scatter_smem<KT, HV>(p);
-    cudaFuncSetAttribute(k_classify<KT, NTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c);
+    cudaFuncSetAttribute(k_classify<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c);
     cudaFuncSetAttribute(k_scatter<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_s);
     const int occ = occupancy(k_scatter<KT, HV>, NTS, sm_s);
     const uint32_t G = std::max<uint32_t>(1, std::min<uint32_t>(gmax, (uint32_t)(c.num_sms * occ)));
     OS_LAUNCH(c.st, c.nested ? "k_classify.sample" : "k_classify",
-              k_classify<KT, NTS><<<G, NTS, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, lb, hist, bid, ntiles));
+              k_classify<KT, HV><<<G, NTS, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, lb, hist, bid, ntiles));
     OS_LAUNCH(c.st, c.nested ? "k_column_scan.sample" : "k_column_scan",
               k_column_scan<<<grid_for((uint64_t)p * 32, 256), 256, 0, c.st>>>(hist, p, G, col, bsize));
     OS_LAUNCH(c.st, c.nested ? "k_bucket_offsets.sample" : "k_bucket_offsets", k_bucket_offsets<<<1, 1024, 0, c.st>>>(bsize, p, boff));

@@ -120,8 +120,8 @@ __global__ void k_pick_splitters(const typename KT::T* __restrict__ tk, const ui
 }
 
 // ---------------------------------------------------------------------------
-// Step 4, pass 1: every CTA owns a contiguous run of units of TOP_SUPER keys
-// (the scatter's tiles, walked here as halves), finds the bucket of each key
+// Step 4, pass 1: every CTA owns a contiguous run of units of SUPER keys
+// (the scatter's units, walked here in tiles of SUB), finds the bucket of each key
 // (tag = its position in the array), stores it in bid (two bytes a key, read
 // back by the scatter instead of searching again) and counts keys per bucket.
 // hist is bucket-major: hist[b * G + g].
@@ -130,12 +130,15 @@ __host__ __device__ inline uint32_t tile_lo(uint32_t g, uint32_t G, uint32_t nti
     return (uint32_t)(((uint64_t)g * ntiles) / G);
 }
 
-template <class KT, int NT>
-__global__ void __launch_bounds__(NT, NT == 512 ? 2 : 3)
+template <class KT, bool HV>
+__global__ void __launch_bounds__(ScatterCfg<typename KT::T, HV>::NT,
+                                  ScatterCfg<typename KT::T, HV>::NT >= 1024 ? 1
+                                  : (ScatterCfg<typename KT::T, HV>::NT == 512 ? 2 : 3))
 k_classify(const typename KT::T* __restrict__ keys, uint32_t n, const typename KT::O* __restrict__ spl_o,
            const uint32_t* __restrict__ spl_t, int p, int lbits, uint32_t* __restrict__ hist,
            uint16_t* __restrict__ bid, uint32_t ntiles) {
     using O = typename KT::O;
+    constexpr int NT = ScatterCfg<typename KT::T, HV>::NT, SUPER = ScatterCfg<typename KT::T, HV>::SUPER;
     extern __shared__ __align__(16) char smem[];
     SplitTable<O> tb;
     tb.bind(smem, p - 1, lbits);
@@ -148,7 +151,7 @@ k_classify(const typename KT::T* __restrict__ keys, uint32_t n, const typename K
     const uint32_t G = gridDim.x, g = blockIdx.x;
     const uint32_t t0 = tile_lo(g, G, ntiles), t1 = tile_lo(g + 1, G, ntiles);
     constexpr int SUB = NT * TOP_IT;
-    for (uint32_t th = t0 * (TOP_SUPER / SUB); th < t1 * (TOP_SUPER / SUB); ++th) {
+    for (uint32_t th = t0 * (SUPER / SUB); th < t1 * (SUPER / SUB); ++th) {
         const uint32_t base = th * SUB + w * (TOP_IT * 32) + lane;
         O o[TOP_IT];
 #pragma unroll
@@ -209,9 +212,9 @@ static __global__ void k_bucket_offsets(const uint32_t* __restrict__ bsize, uint
 }
 
 // ---------------------------------------------------------------------------
-// Step 4, pass 2: the same CTAs walk the same key ranges in tiles of TOP_SUPER
-// keys (512 threads; longer runs per bucket than pass 1's halves, so fewer
-// partly written 32-byte sectors) and move the keys (and payloads) into their
+// Step 4, pass 2: the same CTAs walk the same key ranges in tiles of SUB keys
+// (a whole unit for keys alone, so runs per bucket are as long as the unit
+// allows and fewer 32-byte sectors are partly written) and move the keys (and payloads) into their
 // buckets, using the bucket ids of pass 1.  Keys are
 // staged in shared memory grouped by bucket and written out as contiguous runs.
 // With a payload the scatter is stable: a key's rank among the tile's keys of
@@ -221,7 +224,8 @@ static __global__ void k_bucket_offsets(const uint32_t* __restrict__ bsize, uint
 // shared-memory atomics, one per run of equal neighbours, hand out the slots.
 // ---------------------------------------------------------------------------
 template <class KT, bool HV>
-__global__ void __launch_bounds__(ScatterCfg<typename KT::T, HV>::NT, ScatterCfg<typename KT::T, HV>::NT == 512 ? 2
+__global__ void __launch_bounds__(ScatterCfg<typename KT::T, HV>::NT, ScatterCfg<typename KT::T, HV>::NT >= 1024 ? 1
+                                  : ScatterCfg<typename KT::T, HV>::NT == 512 ? 2
                                   : (sizeof(typename KT::T) == 4 ? 4 : 3))
 k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ vals,
           const uint16_t* __restrict__ bid, uint32_t n, int p, const uint32_t* __restrict__ col,
@@ -229,7 +233,7 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
           uint32_t ntiles, uint32_t* status) {
     using T = typename KT::T;
     using SC = ScatterCfg<typename KT::T, HV>;
-    constexpr int SNT = SC::NT, SWARPS = SC::WARPS, SUB = SC::SUB;
+    constexpr int SNT = SC::NT, SWARPS = SC::WARPS, SUB = SC::SUB, SUPER = SC::SUPER;
     extern __shared__ __align__(16) char smem[];
     char* q = smem;
     T* sk = reinterpret_cast<T*>(q);                 q += sizeof(T) * SUB;
@@ -247,7 +251,7 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint16_t* mycnt = cnt + w * cstride;
     const uint32_t t0 = tile_lo(g, G, ntiles), t1 = tile_lo(g + 1, G, ntiles);
-    for (uint32_t t = t0 * (TOP_SUPER / SUB); t < t1 * (TOP_SUPER / SUB); ++t) {   // tiles of SUB keys
+    for (uint32_t t = t0 * (SUPER / SUB); t < t1 * (SUPER / SUB); ++t) {   // tiles of SUB keys
         const uint32_t tbase = t * SUB;
         const uint32_t base = tbase + w * (TOP_IT * 32) + lane;
         T kv[TOP_IT];
