@@ -178,7 +178,7 @@ void seg_core(Ctx& c, const SegSource& src, const SegClasses& cls, const typenam
     if (B.any_part) {
         const size_t sm_s = seg_scatter_smem<KT, HV>(B.maxp);
         cudaFuncSetAttribute(k_seg_scatter<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_s);
-        constexpr int SNT = SegScatterCfg<HV>::NT;
+        constexpr int SNT = SegScatterCfg<T, HV>::NT;
         const uint32_t g_s = (uint32_t)(c.num_sms * occupancy(k_seg_scatter<KT, HV>, SNT, sm_s));
         OS_LAUNCH(c.st, nest ? "k_seg_scatter.sample" : "k_seg_scatter",
                   k_seg_scatter<KT, HV><<<g_s, SNT, sm_s, c.st>>>(kin, vin, bid, rec, tile0, nseg, tot, hist,

@@ -390,18 +390,19 @@ k_seg_scan(const SegRec* __restrict__ rec, uint32_t nseg, const SegTotals* __res
     }
 }
 
-// Scatter staging: 256 threads stage 2048 keys at a time (measured on GB300: 512
-// threads staging 4096 keys were slower for the bucket phase's ~90 children).
-template <bool HV> struct SegScatterCfg {
+// Scatter staging: 256 threads stage 16 4-byte keys or 8 8-byte keys each at a
+// time (measured on GB300 against 512 threads and the other key counts).
+template <class T, bool HV> struct SegScatterCfg {
     static constexpr int NT = SEG_NT;
+    static constexpr int IT = sizeof(T) == 4 ? 2 * SEG_IT : SEG_IT;
     static constexpr int WARPS = NT / 32;
-    static constexpr int SUB = NT * SEG_IT;
+    static constexpr int SUB = NT * IT;
 };
 
 template <class KT, bool HV>
 size_t seg_scatter_smem(int maxp) {
     using T = typename KT::T;
-    using SC = SegScatterCfg<HV>;
+    using SC = SegScatterCfg<T, HV>;
     size_t b = sizeof(T) * SC::SUB + (HV ? sizeof(uint32_t) * SC::SUB : 0);
     b += sizeof(uint32_t) * (maxp + 1) + sizeof(uint32_t) * maxp + sizeof(uint32_t) * 32;
     b += sizeof(uint16_t) * SC::SUB + (HV ? sizeof(uint16_t) * SC::WARPS * (maxp + 1) : 0);
@@ -414,13 +415,14 @@ size_t seg_scatter_smem(int maxp) {
 // k_scatter (stable with a payload).  Output buffer: out.
 // ---------------------------------------------------------------------------
 template <class KT, bool HV>
-__global__ void __launch_bounds__(SegScatterCfg<HV>::NT, 4)
+__global__ void __launch_bounds__(SegScatterCfg<typename KT::T, HV>::NT, 4)
 k_seg_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ vals,
               const uint16_t* __restrict__ bid, const SegRec* __restrict__ rec, const uint32_t* __restrict__ tile0,
               uint32_t nseg, const SegTotals* __restrict__ tot, const uint32_t* __restrict__ col, int maxp,
               typename KT::T* __restrict__ out, uint32_t* __restrict__ vout, uint32_t* status) {
     using T = typename KT::T;
-    constexpr int SNT = SegScatterCfg<HV>::NT, SWARPS = SegScatterCfg<HV>::WARPS, SUB = SegScatterCfg<HV>::SUB;
+    using SC = SegScatterCfg<T, HV>;
+    constexpr int SNT = SC::NT, SWARPS = SC::WARPS, SUB = SC::SUB, IT = SC::IT;
     extern __shared__ __align__(16) char smem[];
     char* q = smem;
     T* sk = reinterpret_cast<T*>(q);                     q += sizeof(T) * SUB;
@@ -454,11 +456,11 @@ k_seg_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restric
         for (uint32_t sub = 0; sub < r.tile; sub += SUB) {
             const uint32_t lbase = tl * r.tile + sub;
             if (lbase >= tend) break;
-            const uint32_t base = lbase + w * (SEG_IT * 32) + lane;
-            T kv[SEG_IT];
-            uint32_t br[SEG_IT];   // bucket << 16 | rank inside the sub-tile's part of the bucket
+            const uint32_t base = lbase + w * (IT * 32) + lane;
+            T kv[IT];
+            uint32_t br[IT];   // bucket << 16 | rank inside the sub-tile's part of the bucket
 #pragma unroll
-            for (int i = 0; i < SEG_IT; ++i) {
+            for (int i = 0; i < IT; ++i) {
                 const uint32_t e = base + i * 32;
                 kv[i] = e < tend ? keys[r.beg + e] : T(0);
                 br[i] = e < tend ? (uint32_t)bid[r.beg + e] : (uint32_t)p;
@@ -472,7 +474,7 @@ k_seg_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restric
             if (HV) {
                 const int nbits = 32 - __clz(p);
 #pragma unroll
-                for (int i = 0; i < SEG_IT; ++i) {
+                for (int i = 0; i < IT; ++i) {
                     const int b = (int)br[i];
                     const unsigned m = warp_peers((uint32_t)b, nbits);
                     const uint32_t c0 = mycnt[b];
@@ -494,7 +496,7 @@ k_seg_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restric
                 }
             } else {
 #pragma unroll
-                for (int i = 0; i < SEG_IT; ++i) {
+                for (int i = 0; i < IT; ++i) {
                     const uint32_t b = br[i];
                     br[i] = (b << 16) | warp_slot(b, tile_off);
                 }
@@ -502,7 +504,7 @@ k_seg_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restric
             const uint32_t tvalid = block_exclusive_scan(tile_off, p, scratch);
             if (threadIdx.x == 0) tile_off[p] = tvalid;
 #pragma unroll
-            for (int i = 0; i < SEG_IT; ++i) {
+            for (int i = 0; i < IT; ++i) {
                 const int b = (int)(br[i] >> 16);
                 if (b < p) {
                     const uint32_t loc = tile_off[b] + (HV ? mycnt[b] : 0u) + (br[i] & 0xFFFFu);
