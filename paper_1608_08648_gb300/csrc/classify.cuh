@@ -44,6 +44,7 @@ struct SplitTable<uint32_t> : SplitTableBase<uint32_t> {
     __device__ __forceinline__ void set(int i, uint32_t o, uint32_t t) { sc[i] = ((uint64_t)o << 32) | t; }
     __device__ __forceinline__ uint32_t key(int i) const { return (uint32_t)(sc[i] >> 32); }
     // splitter i < (o, t)
+    template <bool LAZY = false>
     __device__ __forceinline__ bool below(int i, uint32_t o, uint32_t t) const {
         return sc[i] < (((uint64_t)o << 32) | t);
     }
@@ -62,8 +63,16 @@ struct SplitTable<uint64_t> : SplitTableBase<uint64_t> {
     }
     __device__ __forceinline__ void set(int i, uint64_t o, uint32_t t) { so[i] = o; st[i] = t; }
     __device__ __forceinline__ uint64_t key(int i) const { return so[i]; }
+    // LAZY: read the tag only when the keys are equal -- fewer shared loads
+    // where a bin holds about one splitter (the bucket phase), more divergent
+    // where bins hold several (measured slower for the top-level classify).
+    template <bool LAZY = false>
     __device__ __forceinline__ bool below(int i, uint64_t o, uint32_t t) const {
         const uint64_t k = so[i];
+        if (LAZY) {
+            if (k != o) return k < o;
+            return st[i] < t;
+        }
         return (k < o) | ((k == o) & (st[i] < t));
     }
 };
@@ -109,7 +118,7 @@ __device__ void split_table_finish(SplitTable<O>& tb, int m, int lbits) {
 }
 
 // Number of splitters strictly below (o, t).
-template <class O>
+template <class O, bool LAZY = false>
 __device__ __forceinline__ int split_find(const SplitTable<O>& tb, O o, uint32_t t) {
     if (tb.m == 0 || o < tb.lo) return 0;
     if (o > tb.hi) return tb.m;
@@ -119,7 +128,7 @@ __device__ __forceinline__ int split_find(const SplitTable<O>& tb, O o, uint32_t
     if (k - j > 4) {
         while (j < k) {
             const int mid = (j + k) >> 1;
-            if (tb.below(mid, o, t)) j = mid + 1;
+            if (tb.template below<LAZY>(mid, o, t)) j = mid + 1;
             else k = mid;
         }
         return j;
@@ -127,7 +136,7 @@ __device__ __forceinline__ int split_find(const SplitTable<O>& tb, O o, uint32_t
     int c = j;
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-        if (j + u < k && tb.below(j + u, o, t)) ++c;   // the splitters below form a prefix
+        if (j + u < k && tb.template below<LAZY>(j + u, o, t)) ++c;   // the splitters below form a prefix
     return c;
 }
 

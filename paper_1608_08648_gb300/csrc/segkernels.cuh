@@ -316,7 +316,7 @@ k_seg_classify(const typename KT::T* __restrict__ keys, const SegRec* __restrict
                 const uint32_t e = base + i * 32;
                 int b = p;                                  // past the end: a spare counter
                 if (e < tend) {
-                    b = split_find<O>(tb, o[i], e);
+                    b = split_find<O, true>(tb, o[i], e);
                     bid[r.beg + e] = (uint16_t)b;
                 }
                 warp_count((uint32_t)b, cnt);
