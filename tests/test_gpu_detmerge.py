@@ -87,3 +87,25 @@ def test_many_pairs_per_tile(kt):
     keys = gen("uniform", n, kt, seed=21)
     st = check(keys, kt, 1024, 1, seed=21)
     assert st["p_used"] == 1024
+
+
+@pytest.mark.parametrize("kt", ["i32", "f64"])
+@pytest.mark.parametrize("dist", ["uniform", "dup", "staggered"])
+def test_full_size_c2_equals_default_path(kt, dist):
+    # C2's size (2^27 keys, p = 1024, r = 16): the split + merge organisation gives the
+    # classify/scatter path's output, splitters and bucket sizes bit for bit, and the
+    # output is ordered (checked on the GPU)
+    n = 1 << 27
+    keys = inputs.keys(dist, n, kt, seed=1, p=1024, device="cuda")
+    a, _, sa = oss.sort(keys, split="det", p=1024, s=16, seed=1, key_type=kt, stats=True)
+    b, _, sb = oss.sort(keys, split="det", p=1024, s=16, seed=1, key_type=kt, stats=True, det_merge=True)
+    torch.cuda.synchronize()
+    view = torch.int64 if kt == "f64" else torch.int32
+    assert torch.equal(a.view(view), b.view(view))
+    assert np.array_equal(sa["bucket_sizes"], sb["bucket_sizes"])
+    assert np.array_equal(sa["spl_tags"], sb["spl_tags"])
+    assert int(sb["max_bucket"]) <= rc.derived_det_bound(n, 1024, 16)
+    if kt == "i32":
+        assert bool((b[1:] >= b[:-1]).all())
+    del a, b, keys
+    torch.cuda.empty_cache()
