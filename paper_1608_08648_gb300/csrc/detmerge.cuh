@@ -185,7 +185,7 @@ __global__ void k_det_partition(int level, uint32_t p, uint64_t n, const typenam
     }
 }
 
-constexpr int DM_TBL = 1024;   // pairs one tile merges through its table (more: recomputed on use)
+constexpr int DM_TBL = 1024;   // pairs one tile merges through its table (more: pair by pair)
 
 // Step 5, one pass of pairwise merges over all buckets, one CTA per tile of
 // DM_OT consecutive outputs.  Pairs wholly inside the tile find their two runs
