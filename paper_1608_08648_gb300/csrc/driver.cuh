@@ -134,13 +134,15 @@ void seg_core(Ctx& c, const SegSource& src, const SegClasses& cls, const typenam
     SegRec* rec = c.ar.take<SegRec>(nseg);
     uint32_t* tile0 = c.ar.take<uint32_t>((size_t)nseg + 1);
     SegTotals* tot = c.ar.take<SegTotals>(1);
+    uint32_t* pseg = c.ar.take<uint32_t>(std::max<uint32_t>(nseg, 1u));
+    uint64_t* pblk = c.ar.take<uint64_t>(3 * (size_t)SEG_PLAN_MAXB);
     O* spl_o = c.ar.take<O>(B.buckets);
     uint32_t* spl_t = c.ar.take<uint32_t>(B.buckets);
     uint32_t* bsize = c.ar.take<uint32_t>(B.buckets);
     uint32_t* hist = B.any_part ? c.ar.take<uint32_t>(B.hist) : nullptr;
     uint16_t* bid = B.any_part ? c.ar.take<uint16_t>(n) : nullptr;
     WorkLists wl{};
-    wl.counts = c.ar.take<uint32_t>(MAX_DEPTH + 1);
+    wl.counts = c.ar.take<uint32_t>(WL_COUNTS);
     wl.part_cap = (uint32_t)(n / CAP + 1);
     wl.leaf_cap = (uint32_t)(B.buckets + (uint64_t)MAX_DEPTH * 6 * wl.part_cap);
     wl.leaf = c.ar.take<WorkItem>(wl.leaf_cap);
@@ -149,10 +151,24 @@ void seg_core(Ctx& c, const SegSource& src, const SegClasses& cls, const typenam
     if (!c.live()) return;
 
     const bool nest = c.nested;
-    os_memset_async(wl.counts, 0, sizeof(uint32_t) * (MAX_DEPTH + 1), c.st);
+    os_memset_async(wl.counts, 0, sizeof(uint32_t) * WL_COUNTS, c.st);
+    os_memset_async(tot, 0, sizeof(SegTotals), c.st);
+    // the plan: CTAs of 1024 threads over ranges of `chunk` segments (one CTA for
+    // up to 1024 segments; more, up to two per SM, for long segment tables)
+    const uint32_t want = std::max<uint32_t>(
+        1u, std::min<uint32_t>((nseg + 1023) / 1024, std::min<uint32_t>(SEG_PLAN_MAXB, 2u * (uint32_t)c.num_sms)));
+    const uint32_t chunk = std::max<uint32_t>(1024u, (uint32_t)((((uint64_t)nseg + want - 1) / want + 1023) / 1024 * 1024));
+    const uint32_t nblk = std::max<uint32_t>(1u, (uint32_t)(((uint64_t)nseg + chunk - 1) / chunk));
     OS_LAUNCH(c.st, nest ? "k_seg_plan.sample" : "k_seg_plan",
-              k_seg_plan<<<1, 1024, 0, c.st>>>(src, cls, seed, rec, tile0, tot, B.tiles, B.buckets, B.hist,
-                                               c.status));
+              k_seg_plan<<<nblk, 1024, 0, c.st>>>(src, cls, seed, rec, tile0, tot, B.tiles, B.buckets, B.hist, chunk,
+                                                  nblk > 1 ? pblk : nullptr, pseg, c.status));
+    if (nblk > 1) {
+        OS_LAUNCH(c.st, nest ? "k_seg_plan.sample" : "k_seg_plan",
+                  k_seg_plan_scan<<<1, SEG_PLAN_MAXB, 0, c.st>>>(pblk, nblk, nseg, tile0, tot, B.tiles, B.buckets,
+                                                                 B.hist, c.status));
+        OS_LAUNCH(c.st, nest ? "k_seg_plan.sample" : "k_seg_plan",
+                  k_seg_plan_apply<<<nblk, 1024, 0, c.st>>>(rec, tile0, nseg, chunk, pblk, tot));
+    }
     const uint32_t gseg = std::max<uint32_t>(1, std::min<uint32_t>(nseg, (uint32_t)c.num_sms * 8));
     if (B.any_part) {
         const size_t sm_spl = sizeof(E) * padded_len<E>(SEG_SAMPLE);
@@ -161,7 +177,7 @@ void seg_core(Ctx& c, const SegSource& src, const SegClasses& cls, const typenam
             nseg, (uint32_t)(c.num_sms * occupancy(k_seg_splitters<KT>, SEG_SPL_NT, sm_spl)));
         OS_LAUNCH(c.st, nest ? "k_seg_splitters.sample" : "k_seg_splitters",
                   k_seg_splitters<KT><<<std::max<uint32_t>(g_spl, 1), SEG_SPL_NT, sm_spl, c.st>>>(
-                      kin, rec, nseg, tot, spl_o, spl_t, c.status));
+                      kin, rec, pseg, tot, spl_o, spl_t, c.status));
         const size_t sm_c = seg_classify_smem<KT>(B.maxp);
         cudaFuncSetAttribute(k_seg_classify<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c);
         const uint32_t g_c = (uint32_t)(c.num_sms * occupancy(k_seg_classify<KT>, SEG_NT, sm_c));
@@ -170,7 +186,7 @@ void seg_core(Ctx& c, const SegSource& src, const SegClasses& cls, const typenam
                                                                    hist, bid));
     }
     OS_LAUNCH(c.st, nest ? "k_seg_scan.sample" : "k_seg_scan",
-              k_seg_scan<<<gseg, SEG_SCAN_NT, 0, c.st>>>(rec, nseg, tot, hist, bsize, wl, CAP,
+              k_seg_scan<<<gseg, SEG_SCAN_NT, 0, c.st>>>(rec, nseg, pseg, tot, hist, bsize, wl, CAP,
                                                          (uint32_t)(static_cast<const void*>(alt) ==
                                                                     static_cast<const void*>(kin)),
                                                          c.status, c.status + 1,
@@ -209,6 +225,9 @@ void seg_core(Ctx& c, const SegSource& src, const SegClasses& cls, const typenam
     const uint32_t grid_l = (uint32_t)(c.num_sms * occupancy(k_leaf<KT, HV>, LNT, leaf_smem));
     OS_LAUNCH(c.st, nest ? "k_leaf.sample" : "k_leaf",
               k_leaf<KT, HV><<<grid_l, LNT, leaf_smem, c.st>>>(false, ss, bufs, wl, inner_seed, c.status));
+    const uint32_t grid_small = (uint32_t)(c.num_sms * occupancy(k_leaf_small<KT, HV>, SMALL_NT, 0));
+    OS_LAUNCH(c.st, nest ? "k_leaf_small.sample" : "k_leaf_small",
+              k_leaf_small<KT, HV><<<grid_small, SMALL_NT, 0, c.st>>>(bufs, wl, n, c.status));
     if (stats) {
         OS_LAUNCH(c.st, "k_seg_export",
                   k_seg_export<KT><<<gseg, 256, 0, c.st>>>(rec, nseg, tot, spl_o, spl_t, bsize, stats->bucket_cap,

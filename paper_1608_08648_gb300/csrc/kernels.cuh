@@ -628,6 +628,25 @@ __device__ __forceinline__ void push_item(WorkItem* list, uint32_t* count, uint3
     else atomicOr(status, ERR_SIZES);
 }
 
+// Leaves of at most SMALL_CAP keys are sorted by one warp each (k_leaf_small)
+// instead of a whole CTA.  They share the leaf array with the larger leaves,
+// filled from its far end (count in wl.counts[SMALL_COUNT]): both kinds come
+// from the same buckets and children, so together they stay within leaf_cap.
+constexpr uint32_t SMALL_CAP = 256;
+constexpr int SMALL_COUNT = MAX_DEPTH + 1;
+constexpr int WL_COUNTS = MAX_DEPTH + 2;   // entries of wl.counts
+
+__device__ __forceinline__ void push_leaf(const WorkLists& wl, uint32_t beg, uint32_t len, uint32_t buf,
+                                          uint32_t* status) {
+    if (len <= SMALL_CAP) {
+        const uint32_t i = atomicAdd(&wl.counts[SMALL_COUNT], 1u);
+        if (i < wl.leaf_cap) wl.leaf[wl.leaf_cap - 1 - i] = WorkItem{beg, len, buf, 0u};
+        else atomicOr(status, ERR_SIZES);
+    } else {
+        push_item(wl.leaf, &wl.counts[0], wl.leaf_cap, beg, len, buf, status);
+    }
+}
+
 // One repartition level d >= 1: walks the list filled by level d - 1 (level 1:
 // by the segmented split).  Persistent: CTAs stride over the work.
 template <class KT, bool HV>
@@ -648,7 +667,7 @@ k_repart(int level, SegSpec ss, SortBufs<KT> bufs, WorkLists wl, uint64_t seed, 
         const uint32_t beg = w.beg, len = w.len, inbuf = w.buf;
         if (len == 0) continue;
         if (len <= (uint32_t)L::CAP) {
-            if (threadIdx.x == 0) push_item(wl.leaf, &wl.counts[0], wl.leaf_cap, beg, len, inbuf, status);
+            if (threadIdx.x == 0) push_leaf(wl, beg, len, inbuf, status);
             continue;
         }
         if ((uint64_t)beg + len > ss.n) {
@@ -664,7 +683,7 @@ k_repart(int level, SegSpec ss, SortBufs<KT> bufs, WorkLists wl, uint64_t seed, 
         for (int b = threadIdx.x; b < p2; b += BK_NT) {
             const uint32_t cb = beg + off[b], cl = off[b + 1] - off[b];
             if (cl == 0) continue;
-            if (cl <= (uint32_t)L::CAP) push_item(wl.leaf, &wl.counts[0], wl.leaf_cap, cb, cl, outbuf, status);
+            if (cl <= (uint32_t)L::CAP) push_leaf(wl, cb, cl, outbuf, status);
             else if (level + 1 < MAX_DEPTH)
                 push_item(next_list, &wl.counts[level + 1], wl.part_cap, cb, cl, outbuf, status);
             else atomicOr(status, ERR_DEPTH);
@@ -704,6 +723,93 @@ k_leaf(bool direct, SegSpec ss, SortBufs<KT> bufs, WorkLists wl, uint64_t seed, 
             continue;
         }
         leaf_sort<KT, HV>(bufs.key_buf(buf), bufs.val_buf(buf), bufs.out, bufs.vout, beg, len, smem);
+    }
+}
+
+// Bitonic sort of a warp's 32 M elements, element m * 32 + lane in x[m] of that
+// lane: exchanges across lanes by shuffles (distance below 32), within a lane
+// in registers (distance 32 and above).  Ascending.
+template <class E, int M>
+__device__ __forceinline__ void warp_bitonic(E (&x)[M]) {
+    const int lane = threadIdx.x & 31;
+    constexpr int N = 32 * M;
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int d = k >> 1; d > 0; d >>= 1) {
+            if (d >= 32) {
+                const int dm = d >> 5;
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    if ((m & dm) == 0) {
+                        if (((m * 32) & k) == 0) cas_up(x[m], x[m + dm]);   // k >= 64: the lane bits do not count
+                        else cas_up(x[m + dm], x[m]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    const E y = E::shfl(x[m], d);
+                    const bool up = ((m * 32 + lane) & k) == 0;
+                    const bool lower = (lane & d) == 0;          // the smaller index of the pair
+                    const bool take_min = lower == up;
+                    const bool y_less = E::lt(y, x[m]);
+                    x[m] = (take_min == y_less) ? y : x[m];
+                }
+            }
+        }
+    }
+}
+
+// One leaf of at most 32 M keys sorted by the calling warp (elements made and
+// read back as in leaf_sort; padding is +infinity).
+template <class KT, bool HV, int M>
+__device__ __forceinline__ void warp_leaf_sort(const typename KT::T* in, const uint32_t* vin, typename KT::T* out,
+                                               uint32_t* vout, uint32_t beg, uint32_t len) {
+    using LE = LeafElem<typename KT::O, HV>;
+    using E = typename LE::E;
+    const uint32_t lane = threadIdx.x & 31;
+    E x[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const uint32_t i = m * 32 + lane;
+        x[m] = i < len ? LE::make(KT::ord(in[beg + i]), i) : EMax<E>::v();
+    }
+    warp_bitonic<E, M>(x);
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const uint32_t i = m * 32 + lane;
+        if (i < len) {
+            out[beg + i] = KT::key(LE::key(x[m]));
+            if (HV) vout[beg + i] = vin[beg + LE::pos(x[m])];
+        }
+    }
+}
+
+// The small leaves (at most SMALL_CAP keys), one warp each, from the far end
+// of the leaf array.  Persistent: warps stride over the items.
+constexpr int SMALL_NT = 256;
+template <class KT, bool HV>
+__global__ void __launch_bounds__(SMALL_NT)
+k_leaf_small(SortBufs<KT> bufs, WorkLists wl, uint64_t n, uint32_t* status) {
+    const uint32_t nfront = min(wl.counts[0], wl.leaf_cap);
+    const uint32_t nsmall = min(wl.counts[SMALL_COUNT], wl.leaf_cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (uint64_t)nfront + nsmall > wl.leaf_cap) atomicOr(status, ERR_SIZES);
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * (SMALL_NT / 32);
+    for (uint32_t it = blockIdx.x * (SMALL_NT / 32) + (threadIdx.x >> 5); it < nsmall; it += warps) {
+        const WorkItem w = wl.leaf[wl.leaf_cap - 1 - it];
+        if (w.len == 0) continue;
+        if (w.len > SMALL_CAP || (uint64_t)w.beg + w.len > n) {
+            if (lane == 0) flag_bounds(status, 14, (uint64_t)w.beg + w.len);
+            continue;
+        }
+        const typename KT::T* in = bufs.key_buf(w.buf);
+        const uint32_t* vin = bufs.val_buf(w.buf);
+        if (w.len <= 32) warp_leaf_sort<KT, HV, 1>(in, vin, bufs.out, bufs.vout, w.beg, w.len);
+        else if (w.len <= 64) warp_leaf_sort<KT, HV, 2>(in, vin, bufs.out, bufs.vout, w.beg, w.len);
+        else if (w.len <= 128) warp_leaf_sort<KT, HV, 4>(in, vin, bufs.out, bufs.vout, w.beg, w.len);
+        else warp_leaf_sort<KT, HV, 8>(in, vin, bufs.out, bufs.vout, w.beg, w.len);
     }
 }
 

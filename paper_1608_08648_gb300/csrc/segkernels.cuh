@@ -70,7 +70,10 @@ struct SegRec {
 
 struct SegTotals {
     uint32_t tiles, buckets, hist, ok;
+    uint32_t nparts;     // segments with p > 1, listed (in no particular order) in the plan's pseg array
 };
+
+constexpr uint32_t SEG_PLAN_MAXB = 1024;    // most CTAs of the plan (one thread each in its block scan)
 
 // Where segment g starts: a 64-bit or 32-bit offset array of nseg + 1 entries,
 // or (neither given) the even split floor(g n / nseg).
@@ -116,11 +119,15 @@ __device__ __forceinline__ uint64_t warp_incl_u64(uint64_t x) {
 }
 
 // ---------------------------------------------------------------------------
-// Plan: one CTA of 1024 threads walks the segments 1024 at a time.
+// Plan: every CTA of 1024 threads walks its range of `chunk` segments 1024 at a
+// time, with offsets relative to the range, and lists the partitioned segments
+// in pseg.  One CTA (blk == nullptr) writes the totals itself; with more, each
+// CTA leaves its three sums in blk for k_seg_plan_scan and k_seg_plan_apply.
 // ---------------------------------------------------------------------------
 static __global__ void __launch_bounds__(1024)
 k_seg_plan(SegSource src, SegClasses cls, uint64_t seed, SegRec* __restrict__ rec, uint32_t* __restrict__ tile0,
-           SegTotals* __restrict__ tot, uint64_t tile_cap, uint64_t bkt_cap, uint64_t hist_cap, uint32_t* status) {
+           SegTotals* __restrict__ tot, uint64_t tile_cap, uint64_t bkt_cap, uint64_t hist_cap, uint32_t chunk,
+           uint64_t* __restrict__ blk, uint32_t* __restrict__ pseg, uint32_t* status) {
     const uint32_t nseg = src.nseg;
     const uint64_t n = src.n;
     __shared__ uint64_t wsum[3][32];
@@ -128,13 +135,15 @@ k_seg_plan(SegSource src, SegClasses cls, uint64_t seed, SegRec* __restrict__ re
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid < 3) carry[tid] = 0;
     const uint64_t state = sm_stream(seed, 2);
-    if (tid == 0 && nseg > 0 && (src.at(0) != 0 || src.at(nseg) != n)) atomicOr(status, ERR_SEGS);
+    if (blockIdx.x == 0 && tid == 0 && nseg > 0 && (src.at(0) != 0 || src.at(nseg) != n)) atomicOr(status, ERR_SEGS);
+    const uint32_t g0 = blockIdx.x * chunk;
+    const uint32_t g1 = (uint64_t)g0 + chunk < nseg ? g0 + chunk : nseg;
     __syncthreads();
-    for (uint32_t base = 0; base < nseg; base += 1024) {
+    for (uint32_t base = g0; base < g1; base += 1024) {
         const uint32_t g = base + tid;
         uint64_t v[3] = {0, 0, 0};
         SegRec r{};
-        if (g < nseg) {
+        if (g < g1) {
             uint64_t a = src.at(g), b = src.at(g + 1);
             if (a > b || b > n) {
                 atomicOr(status, ERR_SEGS);
@@ -182,15 +191,28 @@ k_seg_plan(SegSource src, SegClasses cls, uint64_t seed, SegRec* __restrict__ re
         uint64_t ex[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) ex[q] = carry[q] + incl[q] - v[q] + (w > 0 ? wsum[q][w - 1] : 0);
-        if (g < nseg) {
+        if (g < g1) {
             r.bkt0 = (uint32_t)ex[1];
             r.hist0 = (uint32_t)ex[2];
             rec[g] = r;
             tile0[g] = (uint32_t)ex[0];
         }
+        // the partitioned segments into pseg (one atomic per warp)
+        const bool part = g < g1 && r.p > 1;
+        const unsigned pm = __ballot_sync(0xffffffffu, part);
+        if (pm) {
+            uint32_t at = 0;
+            if (lane == __ffs(pm) - 1) at = atomicAdd(&tot->nparts, (uint32_t)__popc(pm));
+            at = __shfl_sync(0xffffffffu, at, __ffs(pm) - 1);
+            if (part) pseg[at + __popc(pm & lanemask_lt())] = g;
+        }
         __syncthreads();
         if (tid < 3) carry[tid] += wsum[tid][31];
         __syncthreads();
+    }
+    if (blk) {
+        if (tid < 3) blk[3 * (size_t)blockIdx.x + tid] = carry[tid];
+        return;
     }
     if (tid == 0) {
         const bool ok = carry[0] <= tile_cap && carry[1] <= bkt_cap && carry[2] <= hist_cap;
@@ -203,6 +225,58 @@ k_seg_plan(SegSource src, SegClasses cls, uint64_t seed, SegRec* __restrict__ re
     }
 }
 
+// Plan with several CTAs: exclusive scan of the CTAs' sums (in place in blk)
+// and the totals.  One CTA of SEG_PLAN_MAXB threads.
+static __global__ void __launch_bounds__(SEG_PLAN_MAXB)
+k_seg_plan_scan(uint64_t* __restrict__ blk, uint32_t nblk, uint32_t nseg, uint32_t* __restrict__ tile0,
+                SegTotals* __restrict__ tot, uint64_t tile_cap, uint64_t bkt_cap, uint64_t hist_cap, uint32_t* status) {
+    __shared__ uint64_t wsum[3][32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    uint64_t v[3], incl[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        v[q] = (uint32_t)tid < nblk ? blk[3 * (size_t)tid + q] : 0;
+        incl[q] = warp_incl_u64(v[q]);
+        if (lane == 31) wsum[q][w] = incl[q];
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) wsum[q][lane] = warp_incl_u64(lane < (SEG_PLAN_MAXB / 32) ? wsum[q][lane] : 0);
+    }
+    __syncthreads();
+    if ((uint32_t)tid < nblk) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) blk[3 * (size_t)tid + q] = incl[q] - v[q] + (w > 0 ? wsum[q][w - 1] : 0);
+    }
+    if (tid == 0) {
+        const uint64_t t0 = wsum[0][31], t1 = wsum[1][31], t2 = wsum[2][31];
+        const bool ok = t0 <= tile_cap && t1 <= bkt_cap && t2 <= hist_cap;
+        if (!ok) atomicOr(status, ERR_SIZES);
+        tile0[nseg] = ok ? (uint32_t)t0 : 0u;
+        tot->tiles = ok ? (uint32_t)t0 : 0u;
+        tot->buckets = ok ? (uint32_t)t1 : 0u;
+        tot->hist = ok ? (uint32_t)t2 : 0u;
+        tot->ok = ok ? 1u : 0u;
+    }
+}
+
+// Plan with several CTAs: every CTA adds its range's scanned offsets.
+static __global__ void __launch_bounds__(1024)
+k_seg_plan_apply(SegRec* __restrict__ rec, uint32_t* __restrict__ tile0, uint32_t nseg, uint32_t chunk,
+                 const uint64_t* __restrict__ blk, const SegTotals* __restrict__ tot) {
+    if (!tot->ok) return;
+    const uint32_t g0 = blockIdx.x * chunk;
+    const uint32_t g1 = (uint64_t)g0 + chunk < nseg ? g0 + chunk : nseg;
+    const uint32_t o_t = (uint32_t)blk[3 * (size_t)blockIdx.x], o_b = (uint32_t)blk[3 * (size_t)blockIdx.x + 1],
+                   o_h = (uint32_t)blk[3 * (size_t)blockIdx.x + 2];
+    for (uint32_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+        rec[g].bkt0 += o_b;
+        rec[g].hist0 += o_h;
+        tile0[g] += o_t;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Steps 2-3 per segment: positions floor(u_j len / 2^64) for j < p s - 1 from
 // stream 1 of the segment's seed, the tagged sample (key, position) sorted in
@@ -210,7 +284,7 @@ k_seg_plan(SegSource src, SegClasses cls, uint64_t seed, SegRec* __restrict__ re
 // ---------------------------------------------------------------------------
 template <class KT>
 __global__ void __launch_bounds__(SEG_SPL_NT)
-k_seg_splitters(const typename KT::T* __restrict__ keys, const SegRec* __restrict__ rec, uint32_t nseg,
+k_seg_splitters(const typename KT::T* __restrict__ keys, const SegRec* __restrict__ rec, const uint32_t* __restrict__ pseg,
                 const SegTotals* __restrict__ tot, typename KT::O* __restrict__ spl_o,
                 uint32_t* __restrict__ spl_t, uint32_t* status) {
     using O = typename KT::O;
@@ -219,7 +293,9 @@ k_seg_splitters(const typename KT::T* __restrict__ keys, const SegRec* __restric
     extern __shared__ __align__(16) char smem[];
     E* ex = reinterpret_cast<E*>(smem);
     if (!tot->ok) return;
-    for (uint32_t g = blockIdx.x; g < nseg; g += gridDim.x) {
+    const uint32_t nparts = tot->nparts;
+    for (uint32_t i = blockIdx.x; i < nparts; i += gridDim.x) {
+        const uint32_t g = pseg[i];
         const SegRec r = rec[g];
         if (r.p < 2) continue;
         const uint32_t m = r.p * r.s - 1;
@@ -330,8 +406,38 @@ k_seg_classify(const typename KT::T* __restrict__ keys, const SegRec* __restrict
 
 __device__ __forceinline__ void seg_push(const WorkLists& wl, uint32_t beg, uint32_t len, uint32_t buf, uint32_t cap,
                                          uint32_t* status) {
-    if (len <= cap) push_item(wl.leaf, &wl.counts[0], wl.leaf_cap, beg, len, buf, status);
+    if (len <= cap) push_leaf(wl, beg, len, buf, status);
     else push_item(wl.part[0], &wl.counts[1], wl.part_cap, beg, len, buf, status);
+}
+
+// seg_push for a whole warp (every lane calls; lanes with act push one item):
+// one atomic per list per warp.
+__device__ __forceinline__ void seg_push_warp(const WorkLists& wl, bool act, uint32_t beg, uint32_t len, uint32_t buf,
+                                              uint32_t cap, uint32_t* status) {
+    const int lane = threadIdx.x & 31;
+    const int kind = !act ? 0 : (len <= SMALL_CAP ? 1 : (len <= cap ? 2 : 3));
+#pragma unroll
+    for (int kk = 1; kk <= 3; ++kk) {
+        const unsigned m = __ballot_sync(0xffffffffu, kind == kk);
+        if (!m) continue;
+        const int leader = __ffs(m) - 1;
+        uint32_t* cnt = kk == 1 ? &wl.counts[SMALL_COUNT] : (kk == 2 ? &wl.counts[0] : &wl.counts[1]);
+        uint32_t at = 0;
+        if (lane == leader) at = atomicAdd(cnt, (uint32_t)__popc(m));
+        at = __shfl_sync(0xffffffffu, at, leader);
+        if (kind == kk) {
+            const uint32_t i = at + __popc(m & lanemask_lt());
+            const WorkItem it{beg, len, buf, 0u};
+            if (kk == 3) {
+                if (i < wl.part_cap) wl.part[0][i] = it;
+                else atomicOr(status, ERR_SIZES);
+            } else if (i < wl.leaf_cap) {
+                wl.leaf[kk == 1 ? wl.leaf_cap - 1 - i : i] = it;
+            } else {
+                atomicOr(status, ERR_SIZES);
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -345,22 +451,38 @@ __device__ __forceinline__ void seg_push(const WorkLists& wl, uint32_t beg, uint
 // moved / depth_max: keys partitioned here and the repartition depth reached.
 // ---------------------------------------------------------------------------
 static __global__ void __launch_bounds__(SEG_SCAN_NT)
-k_seg_scan(const SegRec* __restrict__ rec, uint32_t nseg, const SegTotals* __restrict__ tot, uint32_t* hist,
-           uint32_t* __restrict__ bsize, WorkLists wl, uint32_t cap, uint32_t src_is_alt, uint32_t* status,
-           uint32_t* depth_max, unsigned long long* moved) {
+k_seg_scan(const SegRec* __restrict__ rec, uint32_t nseg, const uint32_t* __restrict__ pseg,
+           const SegTotals* __restrict__ tot, uint32_t* hist, uint32_t* __restrict__ bsize, WorkLists wl, uint32_t cap,
+           uint32_t src_is_alt, uint32_t* status, uint32_t* depth_max, unsigned long long* moved) {
     __shared__ uint32_t buf[SEG_SCAN_CHUNK];
     __shared__ uint32_t scratch[32];
     if (!tot->ok) return;
-    for (uint32_t g = blockIdx.x; g < nseg; g += gridDim.x) {
-        const SegRec r = rec[g];
-        if (r.p < 2) {
-            if (threadIdx.x == 0) {
+    // segments kept whole: one a thread
+    const uint32_t nthreads = gridDim.x * SEG_SCAN_NT;
+    for (uint32_t g0 = blockIdx.x * SEG_SCAN_NT; g0 < nseg; g0 += nthreads) {
+        const uint32_t g = g0 + threadIdx.x;
+        bool act = false;
+        uint32_t beg = 0, len = 0;
+        if (g < nseg) {
+            const SegRec r = rec[g];
+            if (r.p < 2) {
                 bsize[r.bkt0] = r.len;
                 if (src_is_alt && r.len > cap) atomicOr(status, ERR_SIZES);
-                else if (r.len > 0) seg_push(wl, r.beg, r.len, 0u, cap, status);
+                else if (r.len > 0) {
+                    act = true;
+                    beg = r.beg;
+                    len = r.len;
+                }
             }
-            continue;
         }
+        seg_push_warp(wl, act, beg, len, 0u, cap, status);
+    }
+    // partitioned segments: one a CTA
+    const uint32_t nparts = tot->nparts;
+    for (uint32_t i = blockIdx.x; i < nparts; i += gridDim.x) {
+        const uint32_t g = pseg[i];
+        const SegRec r = rec[g];
+        if (r.p < 2) continue;
         if (threadIdx.x == 0) {
             atomicMax(depth_max, 1u);
             atomicAdd(moved, (unsigned long long)r.len);

@@ -201,3 +201,44 @@ def test_offsets_violation_is_reported_not_faulted():
     assert torch.equal(out[5:20_000], torch.sort(keys[5:20_000]).values)
     assert torch.equal(out[20_000:n - 3], torch.sort(keys[20_000:n - 3]).values)
     assert int(out[0]) == 7 and int(out[n - 1]) == 7
+
+
+def test_largest_segment_count_tiny_and_empty_segments():
+    # OS_SEG_MAX_NSEG segments of 0..7 keys (about one in eight empty), int32 keys
+    # with their index as payload: every segment sorted on its own, stably
+    nseg = B.OS_SEG_MAX_NSEG
+    u = inputs.u64(21, 9, torch.arange(nseg, dtype=torch.int64, device="cuda"))
+    lengths = (u & 7).to(torch.int64)
+    off = torch.zeros(nseg + 1, dtype=torch.int64, device="cuda")
+    off[1:] = torch.cumsum(lengths, 0)
+    n = int(off[-1])
+    keys = inputs.keys("dup", n, "i32", seed=21, device="cuda")
+    vals = torch.arange(n, dtype=torch.int32, device="cuda")
+    out, vout, _ = oss.sort_segmented(keys, off, vals, seed=21)
+    torch.cuda.synchronize()
+    perm = _per_segment_sorted(keys, off, "i32")
+    assert torch.equal(out, keys[perm]), "keys differ from the per-segment stable sort"
+    assert torch.equal(vout, vals[perm]), "payload order differs (stability)"
+    del keys, vals, out, vout, perm
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("kt", ["i32", "u64", "f64"])
+@pytest.mark.parametrize("dist,with_vals", [("dup", True), ("uniform", False)])
+def test_small_leaves_at_warp_sort_boundaries(kt, dist, with_vals):
+    # whole segments of at most 256 keys are sorted by one warp each (bitonic
+    # networks of 32, 64, 128 or 256); lengths around every boundary, and above
+    # 256 (a CTA), each several times
+    base = [1, 2, 3, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 300, 0]
+    lengths = base * 7
+    off = inputs.segment_offsets(torch.tensor(lengths)).cuda()
+    n = int(off[-1])
+    keys = inputs.keys(dist, n, kt, seed=17, device="cuda")
+    vals = torch.arange(n, dtype=torch.int32, device="cuda") if with_vals else None
+    out, vout, _ = oss.sort_segmented(keys, off, vals, seed=17, key_type=kt)
+    torch.cuda.synchronize()
+    perm = _per_segment_sorted(keys, off, kt)
+    view = torch.int32 if kt == "i32" else torch.int64
+    assert torch.equal(out.view(view), keys[perm].view(view))
+    if with_vals:
+        assert torch.equal(vout, vals[perm])
