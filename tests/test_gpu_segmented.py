@@ -229,7 +229,8 @@ def test_small_leaves_at_warp_sort_boundaries(kt, dist, with_vals):
     # whole segments of at most 256 keys are sorted by one warp each (bitonic
     # networks of 32, 64, 128 or 256); lengths around every boundary, and above
     # 256 (a CTA), each several times
-    base = [1, 2, 3, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 300, 0]
+    base = [1, 2, 3, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 300, 0,
+            511, 512, 513, 1023, 1024, 1025, 2000]
     lengths = base * 7
     off = inputs.segment_offsets(torch.tensor(lengths)).cuda()
     n = int(off[-1])
