@@ -160,9 +160,12 @@ int os_workspace_size_host(int key_type, uint64_t n, int has_vals, const os_para
 
 /*
  * Same sort on HOST buffers: copies the keys (and payloads) to the device
- * workspace, sorts, copies the result back and synchronizes the stream.  Host
- * buffers should be pinned for full copy bandwidth; h_keys_out may equal
- * h_keys_in.  Returns OS_ERR_DEVICE if a kernel flagged an error.
+ * workspace, sorts, copies the result back and synchronizes the stream.  From
+ * 2^22 keys on (except 32-byte strings) the buckets are sorted in eight ranges
+ * and each range is copied back, on a stream the library creates once per
+ * device, while the later ranges are still being sorted.  Host buffers should
+ * be pinned for full copy bandwidth; h_keys_out may equal h_keys_in.  Returns
+ * OS_ERR_DEVICE if a kernel flagged an error.
  */
 int os_sort_host(int key_type, const void* h_keys_in, void* h_keys_out,
                  const uint32_t* h_vals_in, uint32_t* h_vals_out, uint64_t n,

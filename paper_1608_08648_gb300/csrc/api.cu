@@ -192,6 +192,61 @@ int fill_stats(int kt, const RunArgs& a, cudaStream_t st, os_stats* stats) {
 
 }  // namespace
 
+namespace {
+
+// os_sort, optionally handing ranges of the output to a HostSink as they finish
+// (a.res.sunk tells whether it did).
+int sort_device(int key_type, const void* d_keys_in, void* d_keys_out, const uint32_t* d_vals_in,
+                uint32_t* d_vals_out, uint64_t n, const os_params* prm, void* d_ws, size_t ws_bytes, void* stream,
+                os_stats* stats, const HostSink* sink, RunArgs& a) {
+    int rc = check_params(key_type, n, prm);
+    if (rc) return rc;
+    if (n > 0 && (!d_keys_in || !d_keys_out)) return OS_ERR_ARG;
+    if ((d_vals_in != nullptr) != (d_vals_out != nullptr)) return OS_ERR_ARG;
+    const bool hv = d_vals_in != nullptr;
+    const size_t need = plan_bytes(key_type, n, hv, prm);
+    if (!d_ws || ws_bytes < need) return OS_ERR_WS;
+    a = RunArgs{};
+    a.kin = d_keys_in;
+    a.kout = d_keys_out;
+    a.vin = d_vals_in;
+    a.vout = d_vals_out;
+    a.has_vals = hv;
+    a.n = n;
+    a.prm = *prm;
+    a.ws = d_ws;
+    a.ws_bytes = ws_bytes;
+    a.st = static_cast<cudaStream_t>(stream);
+    a.num_sms = num_sms_of_current_device();
+    a.sink = sink;
+    rc = dispatch(key_type, a);
+    if (rc) return rc;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (stats) return fill_stats(key_type, a, a.st, stats);
+    return OS_OK;
+}
+
+// The stream on which host-buffer sorts copy finished ranges out (one per device,
+// created on first use), or nullptr.
+cudaStream_t host_copy_stream() {
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        streams[dev] = nullptr;
+    }
+    return streams[dev];
+}
+
+constexpr uint32_t HOST_CHUNKS = 8;            // bucket ranges of a host-buffer sort (measured: 4, 8, 16)
+constexpr uint64_t HOST_CHUNK_MIN_N = 1u << 22;  // below this, one range
+
+}  // namespace
+
 extern "C" {
 
 uint64_t os_launch_count(void) { return g_launches.load(); }
@@ -269,33 +324,12 @@ int os_workspace_size(int key_type, uint64_t n, int has_vals, const os_params* p
     return OS_OK;
 }
 
+
 int os_sort(int key_type, const void* d_keys_in, void* d_keys_out, const uint32_t* d_vals_in, uint32_t* d_vals_out,
             uint64_t n, const os_params* prm, void* d_ws, size_t ws_bytes, void* stream, os_stats* stats) {
-    int rc = check_params(key_type, n, prm);
-    if (rc) return rc;
-    if (n > 0 && (!d_keys_in || !d_keys_out)) return OS_ERR_ARG;
-    if ((d_vals_in != nullptr) != (d_vals_out != nullptr)) return OS_ERR_ARG;
-    const bool hv = d_vals_in != nullptr;
-    const size_t need = plan_bytes(key_type, n, hv, prm);
-    if (!d_ws || ws_bytes < need) return OS_ERR_WS;
     RunArgs a{};
-    a.kin = d_keys_in;
-    a.kout = d_keys_out;
-    a.vin = d_vals_in;
-    a.vout = d_vals_out;
-    a.has_vals = hv;
-    a.n = n;
-    a.prm = *prm;
-    a.ws = d_ws;
-    a.ws_bytes = ws_bytes;
-    a.st = static_cast<cudaStream_t>(stream);
-    a.num_sms = num_sms_of_current_device();
-    rc = dispatch(key_type, a);
-    if (rc) return rc;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e);
-    if (stats) return fill_stats(key_type, a, a.st, stats);
-    return OS_OK;
+    return sort_device(key_type, d_keys_in, d_keys_out, d_vals_in, d_vals_out, n, prm, d_ws, ws_bytes, stream, stats,
+                       nullptr, a);
 }
 
 int os_workspace_size_host(int key_type, uint64_t n, int has_vals, const os_params* prm, size_t* bytes) {
@@ -332,9 +366,18 @@ int os_sort_host(int key_type, const void* h_keys_in, void* h_keys_out, const ui
         if (e == cudaSuccess && hv) e = cudaMemcpyAsync(dv, h_vals_in, n * 4, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e);
     }
-    rc = os_sort(key_type, dk, dk, dv, dv, n, prm, d_ws, inner, stream, nullptr);
+    // the output goes back range by range while the buckets are sorted (32-byte
+    // strings and small inputs: in one copy after the sort)
+    HostSink sink{h_keys_out, h_vals_out, nullptr, 1u};
+    if (key_type != OS_S32 && n >= HOST_CHUNK_MIN_N) {
+        sink.copy = host_copy_stream();
+        sink.chunks = sink.copy ? HOST_CHUNKS : 1u;
+    }
+    RunArgs a{};
+    rc = sort_device(key_type, dk, dk, dv, dv, n, prm, d_ws, inner, stream, nullptr, sink.chunks > 1 ? &sink : nullptr,
+                     a);
     if (rc) return rc;
-    if (n > 0) {
+    if (n > 0 && !a.res.sunk) {
         e = cudaMemcpyAsync(h_keys_out, dk, kbytes, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && hv) e = cudaMemcpyAsync(h_vals_out, dv, n * 4, cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return cuda_fail(e);

@@ -12,6 +12,7 @@
 #pragma once
 
 #include <algorithm>
+#include <vector>
 
 #include "../../include/ossort.h"
 #include "kernels.cuh"
@@ -250,7 +251,7 @@ void segment_sort(Ctx& c, SegSpec ss, const typename KT::T* src, const uint32_t*
     if (ss.nseg == 0 || ss.n == 0) return;
     const bool direct = ss.uniform && (ss.n + ss.nseg - 1) / ss.nseg <= CAP;
     if (!direct) {
-        const SegSource s{nullptr, ss.uniform ? nullptr : ss.off, ss.nseg, ss.n};
+        const SegSource s{nullptr, ss.uniform ? nullptr : ss.off, ss.nseg, ss.n, ss.base};
         seg_core<KT, HV>(c, s, bucket_classes<O>(), src, vsrc, out, vout, alt, valt, seed, nullptr);
         return;
     }
@@ -417,6 +418,18 @@ struct TopResult {
     const uint32_t* det_index = nullptr;   // SqDet with a payload: payloads in the order of the sorted sequences
     void* str_keys = nullptr;              // 32-byte keys: the splitters' keys (device)
     const uint32_t* str_map = nullptr;
+    bool sunk = false;                     // the output already went to a HostSink
+};
+
+// A host-buffer sort copies its output to the host while buckets are still
+// being sorted: the buckets are sorted in `chunks` ranges, and each range's keys
+// (and payloads) are copied on `copy` as soon as that range is done; the
+// caller's stream waits for the copies.
+struct HostSink {
+    void* keys;
+    uint32_t* vals;
+    cudaStream_t copy;
+    uint32_t chunks;
 };
 
 template <class KT, bool HV>
@@ -424,9 +437,65 @@ void det_merge_steps(Ctx& c, const typename KT::T* w1, const uint32_t* vw1, type
                      typename KT::T* kout, uint32_t* vout, uint32_t n, uint32_t p, const typename KT::O* spl_o,
                      const uint32_t* spl_t, uint32_t* boff, uint32_t* bsize);
 
+// Step 5 on buckets [boff[b], boff[b+1]) of src into out: one segmented sort, or,
+// with a HostSink, one per range of buckets, each range copied to the host while
+// the next is sorted.  The measuring pass sizes one sort of all buckets, which
+// bounds every range's (the arena is rewound for each).
+template <class KT, bool HV>
+void sort_buckets(Ctx& c, const uint32_t* boff, uint32_t p, uint32_t n, typename KT::T* src, uint32_t* vsrc,
+                  typename KT::T* out, uint32_t* vout, typename KT::T* alt, uint32_t* valt, uint64_t seed,
+                  const HostSink* sink, TopResult& res) {
+    using T = typename KT::T;
+    if (!sink || sink->chunks < 2 || p < sink->chunks || !sink->copy || c.ar.measure()) {
+        segment_sort<KT, HV>(c, SegSpec::offsets(boff, p, n), src, vsrc, out, vout, alt, valt, seed);
+        return;
+    }
+    if (!c.live()) return;
+    std::vector<uint32_t> hb(p + 1);
+    cudaError_t e = cudaMemcpyAsync(hb.data(), boff, sizeof(uint32_t) * (p + 1), cudaMemcpyDeviceToHost, c.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
+    if (e != cudaSuccess || hb[0] != 0 || hb[p] != n) {   // fall back to one sort, copied by the caller
+        segment_sort<KT, HV>(c, SegSpec::offsets(boff, p, n), src, vsrc, out, vout, alt, valt, seed);
+        return;
+    }
+    const size_t mark = c.ar.used;
+    size_t high = mark;
+    for (uint32_t k = 0; k < sink->chunks; ++k) {
+        const uint32_t b0 = (uint32_t)((uint64_t)k * p / sink->chunks), b1 = (uint32_t)((uint64_t)(k + 1) * p / sink->chunks);
+        const uint32_t base = hb[b0], len = hb[b1] - base;
+        if (len == 0) continue;
+        c.ar.used = mark;
+        segment_sort<KT, HV>(c, SegSpec::offsets_at(boff + b0, b1 - b0, len, base), src + base,
+                             HV ? vsrc + base : nullptr, out + base, HV ? vout + base : nullptr, alt + base,
+                             HV ? valt + base : nullptr, seed);
+        high = std::max(high, c.ar.used);
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            c.ar.failed = true;
+            return;
+        }
+        cudaEventRecord(ev, c.st);
+        cudaStreamWaitEvent(sink->copy, ev, 0);
+        cudaEventDestroy(ev);
+        cudaMemcpyAsync(static_cast<T*>(sink->keys) + base, out + base, sizeof(T) * len, cudaMemcpyDeviceToHost,
+                        sink->copy);
+        if (HV) cudaMemcpyAsync(sink->vals + base, vout + base, sizeof(uint32_t) * len, cudaMemcpyDeviceToHost, sink->copy);
+    }
+    c.ar.used = high;
+    cudaEvent_t done;
+    if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) {
+        c.ar.failed = true;
+        return;
+    }
+    cudaEventRecord(done, sink->copy);
+    cudaStreamWaitEvent(c.st, done, 0);
+    cudaEventDestroy(done);
+    res.sunk = true;
+}
+
 template <class KT, bool HV>
 void sort_top(Ctx& c, const typename KT::T* kin, typename KT::T* kout, const uint32_t* vin, uint32_t* vout,
-              uint32_t n, const os_params& prm, TopResult& res) {
+              uint32_t n, const os_params& prm, TopResult& res, const HostSink* sink = nullptr) {
     using T = typename KT::T;
     using O = typename KT::O;
     const uint32_t p = prm.p, s = prm.s;
@@ -452,7 +521,7 @@ void sort_top(Ctx& c, const typename KT::T* kin, typename KT::T* kout, const uin
     if (prm.split == OS_RAN) {
         splitters_ran<KT>(c, kin, n, p, s, prm.seed, spl_o, spl_t);
         partition_top<KT, HV>(c, kin, vin, n, spl_o, spl_t, p, w1, vw1, boff, bsize);
-        segment_sort<KT, HV>(c, SegSpec::offsets(boff, p, n), w1, vw1, kout, vout, w1, vw1, internal_seed);
+        sort_buckets<KT, HV>(c, boff, p, n, w1, vw1, kout, vout, w1, vw1, internal_seed, sink, res);
     } else {
         T* w2 = c.ar.take<T>(n);
         uint32_t* vw2 = HV ? c.ar.take<uint32_t>(n) : nullptr;
@@ -465,7 +534,7 @@ void sort_top(Ctx& c, const typename KT::T* kin, typename KT::T* kout, const uin
             det_merge_steps<KT, HV>(c, w1, vw1, w2, vw2, kout, vout, n, p, spl_o, spl_t, boff, bsize);
         } else {
             partition_top<KT, HV>(c, w1, vw1, n, spl_o, spl_t, p, w2, vw2, boff, bsize);
-            segment_sort<KT, HV>(c, SegSpec::offsets(boff, p, n), w2, vw2, kout, vout, w2, vw2, internal_seed);
+            sort_buckets<KT, HV>(c, boff, p, n, w2, vw2, kout, vout, w2, vw2, internal_seed, sink, res);
         }
     }
 }
@@ -483,6 +552,7 @@ struct RunArgs {
     size_t ws_bytes;
     cudaStream_t st;
     int num_sms;
+    const HostSink* sink;   // host-buffer sorts: where ranges of the output go as they finish
     // outputs
     size_t used;
     uint32_t* status;
@@ -501,8 +571,8 @@ int run_sort(RunArgs& a) {
     if (c.live()) os_memset_async(c.status, 0, 8 * sizeof(uint32_t), c.st);
     const T* kin = static_cast<const T*>(a.kin);
     T* kout = static_cast<T*>(a.kout);
-    if (a.has_vals) sort_top<KT, true>(c, kin, kout, a.vin, a.vout, (uint32_t)a.n, a.prm, a.res);
-    else sort_top<KT, false>(c, kin, kout, nullptr, nullptr, (uint32_t)a.n, a.prm, a.res);
+    if (a.has_vals) sort_top<KT, true>(c, kin, kout, a.vin, a.vout, (uint32_t)a.n, a.prm, a.res, a.sink);
+    else sort_top<KT, false>(c, kin, kout, nullptr, nullptr, (uint32_t)a.n, a.prm, a.res, a.sink);
     a.used = c.ar.used;
     a.status = c.status;
     return c.ar.failed ? OS_ERR_WS : OS_OK;

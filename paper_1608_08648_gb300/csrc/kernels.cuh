@@ -351,7 +351,11 @@ struct SegSpec {
     uint32_t nseg;
     uint32_t uniform;      // 1: segment k = [floor(kn/nseg), floor((k+1)n/nseg)); off unused
     uint64_t n;            // length of the array the segments tile
+    uint64_t base = 0;     // off[k] - base is the offset (off[0] == base); the bucket phase only
     static SegSpec offsets(const uint32_t* o, uint32_t nseg, uint64_t n) { return SegSpec{o, nseg, 0u, n}; }
+    static SegSpec offsets_at(const uint32_t* o, uint32_t nseg, uint64_t n, uint64_t base) {
+        return SegSpec{o, nseg, 0u, n, base};
+    }
     static SegSpec even(uint32_t nseg, uint64_t n) { return SegSpec{nullptr, nseg, 1u, n}; }
 };
 

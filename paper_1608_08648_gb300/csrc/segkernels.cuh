@@ -82,9 +82,10 @@ struct SegSource {
     const uint32_t* off32;
     uint32_t nseg;
     uint64_t n;
+    uint64_t base = 0;   // subtracted from the given offsets (a range of a larger table)
     __device__ __forceinline__ uint64_t at(uint32_t g) const {
-        if (off64) return off64[g];
-        if (off32) return off32[g];
+        if (off64) return off64[g] - base;
+        if (off32) return off32[g] - base;
         return (uint64_t)g * n / nseg;
     }
 };
