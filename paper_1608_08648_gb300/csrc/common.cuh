@@ -78,14 +78,13 @@ constexpr int TOP_TILE = TOP_NT * TOP_IT;
 constexpr int TOP_WARPS = TOP_NT / 32;
 // Top-level classify and scatter.  SUPER is the unit both passes walk (a CTA
 // owns a contiguous run of units).  Keys alone are staged a whole unit at a
-// time: 4-byte keys by 512 threads (8192 keys), 8-byte keys by 1024 threads
-// (16384 keys: longer runs per bucket, fewer partly written 32-byte sectors;
-// measured faster for 8-byte keys only).  Payload sorts (whose per-warp
+// time by 512 threads (8192 keys: runs of twice as many keys per bucket as
+// halves, fewer partly written 32-byte sectors).  Payload sorts (whose per-warp
 // stable-ranking counters must fit shared memory for p up to MAX_P) use 256
 // threads and 8192-key units in two halves.  Classify uses the same thread
 // count, since both passes split the array among the same number of CTAs.
 template <class T, bool HV> struct ScatterCfg {
-    static constexpr int NT = HV ? TOP_NT : (sizeof(T) == 4 ? 2 * TOP_NT : 4 * TOP_NT);
+    static constexpr int NT = HV ? TOP_NT : 2 * TOP_NT;
     static constexpr int WARPS = NT / 32;
     static constexpr int SUB = NT * TOP_IT;
     static constexpr int SUPER = SUB > 2 * TOP_TILE ? SUB : 2 * TOP_TILE;

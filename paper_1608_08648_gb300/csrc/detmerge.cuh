@@ -387,7 +387,7 @@ void det_merge_steps(Ctx& c, const typename KT::T* w1, const uint32_t* vw1, type
     int passes = 0;
     while ((1u << passes) < p) ++passes;
     const size_t sm = det_merge_smem<KT, HV>();
-    cudaFuncSetAttribute(k_det_merge<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    smem_at_least(reinterpret_cast<const void*>(k_det_merge<KT, HV>), sm);
     const uint32_t ntiles = (uint32_t)(((uint64_t)n + DM_OT - 1) / DM_OT);
     // the pieces into their buckets: into the buffer the first merge pass reads
     typename KT::T* lay = ((passes - 1) % 2 == 0) ? w2 : kout;

@@ -12,6 +12,9 @@
 #pragma once
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "../../include/ossort.h"
@@ -47,6 +50,21 @@ inline unsigned grid_for(uint64_t work, int threads, unsigned cap = 4096) {
 }
 
 constexpr uint32_t G_CAP = 2048;   // most CTAs of the grid-wide classify / scatter
+
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`, never lower
+// it.  The limit belongs to the kernel, not to a call: sorts running at once on
+// other host threads with other p would otherwise set it back below what a launch
+// of this one, already queued, needs.  One limit per (device, kernel), under a lock.
+inline void smem_at_least(const void* fn, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> cur;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& c = cur[{dev, fn}];
+    if (bytes > c && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
+        c = bytes;
+}
 
 template <class K>
 int occupancy(K kernel, int threads, size_t smem) {
@@ -173,14 +191,14 @@ void seg_core(Ctx& c, const SegSource& src, const SegClasses& cls, const typenam
     const uint32_t gseg = std::max<uint32_t>(1, std::min<uint32_t>(nseg, (uint32_t)c.num_sms * 8));
     if (B.any_part) {
         const size_t sm_spl = sizeof(E) * padded_len<E>(SEG_SAMPLE);
-        cudaFuncSetAttribute(k_seg_splitters<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_spl);
+        smem_at_least(reinterpret_cast<const void*>(k_seg_splitters<KT>), sm_spl);
         const uint32_t g_spl = std::min<uint32_t>(
             nseg, (uint32_t)(c.num_sms * occupancy(k_seg_splitters<KT>, SEG_SPL_NT, sm_spl)));
         OS_LAUNCH(c.st, nest ? "k_seg_splitters.sample" : "k_seg_splitters",
                   k_seg_splitters<KT><<<std::max<uint32_t>(g_spl, 1), SEG_SPL_NT, sm_spl, c.st>>>(
                       kin, rec, pseg, tot, spl_o, spl_t, c.status));
         const size_t sm_c = seg_classify_smem<KT>(B.maxp);
-        cudaFuncSetAttribute(k_seg_classify<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c);
+        smem_at_least(reinterpret_cast<const void*>(k_seg_classify<KT>), sm_c);
         const uint32_t g_c = (uint32_t)(c.num_sms * occupancy(k_seg_classify<KT>, SEG_NT, sm_c));
         OS_LAUNCH(c.st, nest ? "k_seg_classify.sample" : "k_seg_classify",
                   k_seg_classify<KT><<<g_c, SEG_NT, sm_c, c.st>>>(kin, rec, tile0, nseg, tot, spl_o, spl_t, B.maxp,
@@ -194,7 +212,7 @@ void seg_core(Ctx& c, const SegSource& src, const SegClasses& cls, const typenam
                                                          reinterpret_cast<unsigned long long*>(c.status + 2)));
     if (B.any_part) {
         const size_t sm_s = seg_scatter_smem<KT, HV>(B.maxp);
-        cudaFuncSetAttribute(k_seg_scatter<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_s);
+        smem_at_least(reinterpret_cast<const void*>(k_seg_scatter<KT, HV>), sm_s);
         constexpr int SNT = SegScatterCfg<T, HV>::NT;
         const uint32_t g_s = (uint32_t)(c.num_sms * occupancy(k_seg_scatter<KT, HV>, SNT, sm_s));
         OS_LAUNCH(c.st, nest ? "k_seg_scatter.sample" : "k_seg_scatter",
@@ -212,7 +230,7 @@ void seg_core(Ctx& c, const SegSource& src, const SegClasses& cls, const typenam
     bufs.vout = vout;
     const SegSpec ss{nullptr, 0u, 0u, n};
     using L = BucketSmem<KT, HV>;
-    cudaFuncSetAttribute(k_repart<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+    smem_at_least(reinterpret_cast<const void*>(k_repart<KT, HV>), L::bytes);
     const uint32_t grid_r = (uint32_t)(c.num_sms * occupancy(k_repart<KT, HV>, BK_NT, L::bytes));
     const uint64_t inner_seed = sm_mix(seed ^ 0x5E6D5E6Dull);
     for (int level = 1; level < MAX_DEPTH; ++level)
@@ -221,7 +239,7 @@ void seg_core(Ctx& c, const SegSource& src, const SegClasses& cls, const typenam
                                                                       c.status + 1,
                                                                       reinterpret_cast<unsigned long long*>(c.status + 4)));
     const size_t leaf_smem = LeafSmem<KT, HV>::bytes;
-    cudaFuncSetAttribute(k_leaf<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf_smem);
+    smem_at_least(reinterpret_cast<const void*>(k_leaf<KT, HV>), leaf_smem);
     constexpr int LNT = LeafCfg<O, HV>::NT;
     const uint32_t grid_l = (uint32_t)(c.num_sms * occupancy(k_leaf<KT, HV>, LNT, leaf_smem));
     OS_LAUNCH(c.st, nest ? "k_leaf.sample" : "k_leaf",
@@ -263,7 +281,7 @@ void segment_sort(Ctx& c, SegSpec ss, const typename KT::T* src, const uint32_t*
     bufs.vout = vout;
     const WorkLists wl{};
     const size_t leaf_smem = LeafSmem<KT, HV>::bytes;
-    cudaFuncSetAttribute(k_leaf<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf_smem);
+    smem_at_least(reinterpret_cast<const void*>(k_leaf<KT, HV>), leaf_smem);
     constexpr int LNT = LeafCfg<O, HV>::NT;
     const uint32_t grid_l = (uint32_t)(c.num_sms * occupancy(k_leaf<KT, HV>, LNT, leaf_smem));
     OS_LAUNCH(c.st, c.nested ? "k_leaf.sample" : "k_leaf",
@@ -310,8 +328,8 @@ void partition_top(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, uint
     if (!c.live()) return;
     constexpr int NTS = ScatterCfg<typename KT::T, HV>::NT;
     const size_t sm_c = classify_smem<KT>(p, lb), sm_s = scatter_smem<KT, HV>(p);
-    cudaFuncSetAttribute(k_classify<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c);
-    cudaFuncSetAttribute(k_scatter<KT, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_s);
+    smem_at_least(reinterpret_cast<const void*>(k_classify<KT, HV>), sm_c);
+    smem_at_least(reinterpret_cast<const void*>(k_scatter<KT, HV>), sm_s);
     const int occ = occupancy(k_scatter<KT, HV>, NTS, sm_s);
     const uint32_t G = std::max<uint32_t>(1, std::min<uint32_t>(gmax, (uint32_t)(c.num_sms * occ)));
     OS_LAUNCH(c.st, c.nested ? "k_classify.sample" : "k_classify",
