@@ -126,3 +126,33 @@ def test_refusals_and_shutdown_with_queued_work():
     assert st["queued"] == 1 and st["inflight"] == 0    # t1's output is still held
     srv.close()                                         # t2 never admitted: dropped
     del t2
+
+
+def test_concurrent_host_threads_with_different_p():
+    # two host threads sort float64 keys at once, each on its own stream, with
+    # different p (so the same kernels need different shared memory); every result
+    # must be the sorted input (the keys hold no negative zero, so torch's order is
+    # the total order)
+    import threading
+    big = inputs.keys("uniform", 1 << 20, "f64", seed=1, device="cuda")
+    small = inputs.keys("dup", 30_000, "f64", seed=2, device="cuda")
+    truth = {id(big): as_int(torch.sort(big).values), id(small): as_int(torch.sort(small).values)}
+    torch.cuda.synchronize()
+    wrong = []
+
+    def worker(keys, p, reps):
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            for r in range(reps):
+                out, _, _ = oss.sort(keys, split="ran", p=p, s=16, seed=r, key_type="f64")
+                st.synchronize()
+                if not torch.equal(as_int(out), truth[id(keys)]):
+                    wrong.append((p, r))
+
+    threads = [threading.Thread(target=worker, args=(big, 1024, 24)),
+               threading.Thread(target=worker, args=(small, 4, 120))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not wrong, f"wrong results (p, repetition): {wrong[:8]}"
