@@ -16,7 +16,12 @@
  *
  * Conventions shared by every entry point:
  *  - Device pointers are plain CUDA device (or managed) addresses.  The caller
- *    owns every buffer; the library never allocates device or pinned memory.
+ *    owns every buffer; the sort entry points allocate no memory (the server
+ *    keeps a small pinned status array per in-flight slot, os_sort_noalloc a
+ *    static device array, and os_sort_host one copy stream per device).
+ *  - Calls may come from several host threads at once, each with its own
+ *    workspace: a kernel's shared-memory limit is only ever raised, so
+ *    concurrent calls with different p do not interfere.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Work is enqueued on it and the call returns without waiting, except where
  *    an entry point says it synchronizes.
