@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--p", type=int, default=None,
                     help="buckets (default: 512 for int32 keys, 1024 for 8-byte keys; the fastest on GB300)")
     ap.add_argument("--s", type=int, default=16)
+    ap.add_argument("--p-f64", type=int, default=1024, help="p of the float64 sub-record of the int32 line")
+    ap.add_argument("--no-f64", action="store_true", help="leave the float64 sub-record out of the int32 line")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--det-merge", action="store_true",
                     help="SqDet with steps 4-5 as in Algorithm 1 (split the sorted sequences, merge every bucket)")
@@ -68,10 +70,10 @@ def parse():
     return ap.parse_args()
 
 
-def workload_name(a, n):
+def workload_name(a, n, dtype=None, p=None):
     org = ", steps 4-5 as split + merge" if a.det_merge else ""
-    return (f"n={n} ({'2^%d' % (n.bit_length() - 1) if n & (n - 1) == 0 else n}) {a.dtype} {a.dist} "
-            f"seed {a.seed}, Sq{'Ran' if a.split == 'ran' else 'Det'} p={a.p} s={a.s}{org}")
+    return (f"n={n} ({'2^%d' % (n.bit_length() - 1) if n & (n - 1) == 0 else n}) {dtype or a.dtype} {a.dist} "
+            f"seed {a.seed}, Sq{'Ran' if a.split == 'ran' else 'Det'} p={p or a.p} s={a.s}{org}")
 
 
 def measured_peaks():
@@ -541,8 +543,31 @@ def run_serving(a, rank, world, local, count, saturation=1000):
     sat = srv.replay(reqs[:m], [0.0] * m)
     sat_span = max(r.done_s for r in sat) - min(r.submit_s for r in sat)
     sat_keys = sum(trace["n"][:m])
+
+    # the same trace with every request's keys in pinned host memory: the server
+    # copies them in when it admits the request (OS_REQ_HOST_INPUT), so each
+    # latency includes that request's host-to-device copy
+    hsrc = {k: v.cpu().pin_memory() for k, v in src.items()}
+
+    def hreq(i):
+        dt, dist, n, off = trace["dtype"][i], trace["dist"][i], trace["n"][i], trace["offset"][i]
+        return srv.request(hsrc[(dt, dist)][off:off + n], "ran", SERVE["p"], SERVE["s"], trace["req_seed"][i], dt)
+
+    hreqs = [hreq(i) for i in range(count)]
+    hw = srv.replay(hreqs[:16], [0.0] * min(16, count))
+    assert all(r.status == 0 for r in hw)
+    hout = srv.replay(hreqs, trace["arrival_s"])
+    assert all(r.status == 0 for r in hout), "a host-input request failed"
+    hlat = [(r.done_s - r.submit_s) * 1e3 for r in hout]
+    hspan = max(r.done_s for r in hout) - min(r.submit_s for r in hout)
+    h2d = {"value": world * keys_total / hspan, "unit": "keys/s",
+           "latency_ms": {"p50": _quantile(hlat, 0.5), "p90": _quantile(hlat, 0.9), "p99": _quantile(hlat, 0.99),
+                          "max": max(hlat), "mean": sum(hlat) / len(hlat)},
+           "h2d_bytes": int(sum(n * KEY_BYTES[dt] for n, dt in zip(trace["n"], trace["dtype"]))),
+           "note": "same trace and arrival times; keys in pinned host memory, copied in by the server on the "
+                   "request's stream after admission (OS_REQ_HOST_INPUT); outputs stay on the device"}
     srv.close()
-    del src
+    del src, hsrc
     torch.cuda.empty_cache()
     return {"requests": count, "keys": keys_total, "span_s": span, "value": world * sustained,
             "offered": keys_total / trace["arrival_s"][-1],
@@ -552,7 +577,7 @@ def run_serving(a, rank, world, local, count, saturation=1000):
             "capacity": {"value": world * sat_keys / sat_span, "requests": m,
                          "note": "the first requests of the trace submitted at once"},
             "arena_peak_gb": st["arena_peak"] / 1e9, "max_inflight_seen": st["max_inflight_seen"],
-            "gpu_launches": launches, "clocks": clk}
+            "gpu_launches": launches, "clocks": clk, "h2d": h2d}
 
 
 def run_serving_line(a, rank, world, local):
@@ -566,8 +591,8 @@ def run_serving_line(a, rank, world, local):
            "latency_ms": sv["latency_ms"], "queue_wait_ms": sv["queue_wait_ms"], "offered": sv["offered"],
            "capacity": sv["capacity"], "arena_peak_gb": sv["arena_peak_gb"],
            "max_inflight_seen": sv["max_inflight_seen"], "roofline": None,
-           "e2e": None, "e2e_note": "requests arrive with their keys resident on the device (the workload's "
-                                    "definition); the host-copy variant is measured by the sort line's e2e",
+           "e2e": {"value": sv["h2d"]["value"], "unit": "keys/s", "h2d_bytes_per_step": sv["h2d"]["h2d_bytes"],
+                   "d2h_bytes_per_step": 0, "latency_ms": sv["h2d"]["latency_ms"], "note": sv["h2d"]["note"]},
            "gpu_launches": sv["gpu_launches"], "clocks": sv["clocks"]}
     return res
 
@@ -747,21 +772,42 @@ def run_strings_line(a, rank, world, local):
 
 # ---- our arm ------------------------------------------------------------------------
 
-def run_ours(a, rank, world, local):
-    import numpy as np
+def host_link_gbs(h_buf, d_buf, stream, reps=3):
+    """Plain copy rates of the pinned host buffer the e2e leg uses, GB/s each way
+    (host to device, device to host), timed with CUDA events: the rate the e2e
+    number's copies are bound by on this machine."""
+    import torch
+    res = []
+    for src, dst in ((h_buf, d_buf), (d_buf, h_buf)):
+        dst.copy_(src, non_blocking=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            dst.copy_(src, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res.append(round(reps * src.numel() * src.element_size() / (e0.elapsed_time(e1) / 1e3) / 1e9, 1))
+    return res
+
+
+def time_sort(a, dtype, p, rank, world, local, steps, warmup, with_e2e=True):
+    """One key type's sort of the configured n: the timed region (profiler off),
+    a second pass of the same steps with the library's per-launch event profiler
+    on (per-kernel device times, dominant kernel, roofline), the statistics of one
+    untimed sort, and the end-to-end variant through host buffers."""
     import torch
 
     import paper_1608_08648_gb300 as oss
     from paper_1608_08648_gb300 import inputs
 
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n = a.keys
-    kt = oss.KEY_TYPES[a.dtype]
-    kb, vb = KEY_BYTES[a.dtype], 0
-    keys = inputs.keys(a.dist, n, a.dtype, seed=a.seed + rank, p=a.p, device=dev)
+    kt = oss.KEY_TYPES[dtype]
+    kb, vb = KEY_BYTES[dtype], 0
+    keys = inputs.keys(a.dist, n, dtype, seed=a.seed + rank, p=p, device=dev)
     out = torch.empty_like(keys)
-    prm = oss.params(a.split, a.p, a.s, a.seed, oss.OS_STABLE | (2 if a.det_merge else 0))
+    prm = oss.params(a.split, p, a.s, a.seed, oss.OS_STABLE | (2 if a.det_merge else 0))
     rc, need = oss.os_workspace_size(kt, n, False, prm)
     assert rc == 0, oss.os_strerror(rc)
     ws = torch.empty(need, dtype=torch.uint8, device=dev)
@@ -773,77 +819,107 @@ def run_ours(a, rank, world, local):
         if r != 0:
             raise RuntimeError(f"os_sort failed: {oss.os_strerror(r)} (cuda {oss.os_last_cuda_error()})")
 
-    for _ in range(a.warmup):
+    for _ in range(warmup):
         step()
     rc, bits = oss.os_check(ws.data_ptr(), sh)
     assert rc == 0 and bits == 0, f"device status {bits:#x}"
     # correctness of the last warm-up output (not timed): ordered and a permutation
-    ok = out.view(torch.int64) if a.dtype == "u64" else out
-    if a.dtype == "f64":
+    ok = out.view(torch.int64) if dtype == "u64" else out
+    if dtype == "f64":
         b = out.view(torch.int64)
         ordk = torch.where(b < 0, b ^ torch.iinfo(torch.int64).max, b)   # signed-comparable totalOrder
         assert bool((ordk[1:] >= ordk[:-1]).all()), "output not ordered"
-    elif a.dtype == "i32":
+        del b, ordk
+    elif dtype == "i32":
         assert bool((ok[1:] >= ok[:-1]).all()), "output not ordered"
-    assert torch.equal(torch.sort(keys.view(torch.int64) if a.dtype != "i32" else keys).values,
-                       torch.sort(out.view(torch.int64) if a.dtype != "i32" else out).values), "not a permutation"
+    assert torch.equal(torch.sort(keys.view(torch.int64) if dtype != "i32" else keys).values,
+                       torch.sort(out.view(torch.int64) if dtype != "i32" else out).values), "not a permutation"
     # statistics of one untimed sort: repartitioned keys (for the byte ledger)
-    _, _, st = oss.sort(keys, split=a.split, p=a.p, s=a.s, seed=a.seed, out=out, workspace=ws, key_type=a.dtype,
+    _, _, st = oss.sort(keys, split=a.split, p=p, s=a.s, seed=a.seed, out=out, workspace=ws, key_type=dtype,
                         stats=True, det_merge=a.det_merge)
     torch.cuda.synchronize()
     _, ctr = oss.os_read_counters(ws.data_ptr(), sh)
     split_keys = ctr["split_keys"]
 
+    # the timed region: K sorts back to back, no per-launch instrumentation
     clocks = Clocks(local)
     barrier(world)
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
     launches0 = oss.os_launch_count()
-    oss.os_profile_start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(a.steps):
+    for _ in range(steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
-    rc, prof = oss.os_profile_stop()
     launches = oss.os_launch_count() - launches0
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / a.steps
+    ms = e0.elapsed_time(e1) / steps
     ms = max_over_ranks(ms, world)
     value = world * n / (ms / 1e3)
 
+    # per-kernel device times: the same K sorts again with every launch bracketed by
+    # a CUDA event pair on its stream (os_profile_start / os_profile_stop)
+    oss.os_profile_start()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(steps):
+        step()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    rc, prof = oss.os_profile_stop()
+    prof_ms = p0.elapsed_time(p1) / steps
+
     # e2e: the same sort through the host-buffer entry point, copies included
     e2e = None
-    if not a.no_e2e:
+    if with_e2e:
         h_in = keys.cpu().pin_memory()
         h_out = torch.empty_like(h_in).pin_memory()
         rc, hneed = oss.os_workspace_size_host(kt, n, False, prm)
-        hws = torch.empty(hneed, dtype=torch.uint8, device=dev)
         del ws
         torch.cuda.empty_cache()
+        hws = torch.empty(hneed, dtype=torch.uint8, device=dev)
+        probe = torch.empty_like(out)
+        link = host_link_gbs(h_in, probe, stream)
+        del probe
         for _ in range(2):
             r = oss.os_sort_host(kt, h_in.data_ptr(), h_out.data_ptr(), None, None, n, prm, hws.data_ptr(), hneed,
                                  sh)
             assert r == 0, oss.os_strerror(r)
         barrier(world)
-        k2 = max(2, min(a.steps, 5))
+        k2 = max(2, min(steps, 5))
+        h0 = torch.cuda.Event(enable_timing=True)
+        h1 = torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
+        h0.record(stream)
         for _ in range(k2):
             r = oss.os_sort_host(kt, h_in.data_ptr(), h_out.data_ptr(), None, None, n, prm, hws.data_ptr(), hneed,
                                  sh)
             assert r == 0, oss.os_strerror(r)
+        h1.record(stream)
+        torch.cuda.synchronize()
         t = (time.perf_counter() - t0) / k2
         t = max_over_ranks(t, world)
+        # the device sort of the same keys (out) is the reference for the host result
         assert torch.equal(h_out, out.cpu()), "e2e output differs from the device-resident sort"
         e2e = {"value": world * n / t, "unit": "keys/s", "ms_per_step": t * 1e3,
-               "h2d_bytes_per_step": n * kb, "d2h_bytes_per_step": n * kb}
+               "h2d_bytes_per_step": n * kb, "d2h_bytes_per_step": n * kb,
+               "host_link_gbs": {"h2d": link[0], "d2h": link[1],
+                                 "note": "plain pinned copies of the same buffers in the same run; the e2e time is "
+                                         "bounded below by the copy-in plus the part of the copy-out that does not "
+                                         "overlap the bucket sorts"},
+               "ms_device_events": round(h0.elapsed_time(h1) / k2, 3)}
+        del hws
+    else:
+        del ws
 
     # context: torch.sort (CUB radix sort, values and int64 indices) of the same keys
-    tk = keys.view(torch.int64) if a.dtype == "u64" else keys
+    tk = keys.view(torch.int64) if dtype == "u64" else keys
     for _ in range(2):
         torch.sort(tk)
     t0e = torch.cuda.Event(enable_timing=True)
@@ -854,43 +930,77 @@ def run_ours(a, rank, world, local):
     t1e.record(stream)
     torch.cuda.synchronize()
     torch_sort_ms = t0e.elapsed_time(t1e) / 3
+    del tk, keys, out
+    torch.cuda.empty_cache()
 
-    # roofline of the dominant kernel (top-level launches only)
+    # roofline of the dominant kernel (top-level launches only), from the profiled pass
     peaks, peak_kind = measured_peaks()
     top = [k for k in prof if not k["name"].endswith(".sample")]
     dom = max(top, key=lambda k: k["total_ms"]) if top else None
     roof = None
     if dom:
-        alg = algorithmic_bytes(dom["name"], n, kb, vb, st["repart_keys"], split_keys) * a.steps
+        alg = algorithmic_bytes(dom["name"], n, kb, vb, st["repart_keys"], split_keys) * steps
         achieved = alg / (dom["total_ms"] / 1e3) / 1e9 if dom["total_ms"] > 0 else 0.0
         peak = float(peaks["hbm_gbs"])
         roof = {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": measured_traffic(dom["name"], a.dtype, n),
+                "traffic": measured_traffic(dom["name"], dtype, n),
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "avg_launch_ms": round(dom["total_ms"] / dom["launches"], 4),
                 "alg_bytes_per_step": algorithmic_bytes(dom["name"], n, kb, vb, st["repart_keys"], split_keys),
-                "pipeline": pipeline_ledger(n, kb, vb, split_keys, st["repart_keys"], ms, peak, a.dtype, a.p)}
+                "timing": "CUDA events around every launch of the kernel on its stream, in a second pass of the "
+                          "same steps with the library's event profiler on",
+                "pipeline": pipeline_ledger(n, kb, vb, split_keys, st["repart_keys"], ms, peak, dtype, p)}
+    return {"n": n, "dtype": dtype, "p": p, "value": value, "ms": ms, "roofline": roof, "e2e": e2e,
+            "launches": launches, "clocks": clk, "prof": prof, "prof_ms": prof_ms, "stats": st,
+            "split_keys": split_keys, "torch_sort_ms": torch_sort_ms}
 
-    res = {"metric": "keys/s", "value": value, "unit": "keys/s", "n_gpus": world, "steps": a.steps,
-           "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+
+def sort_summary(a, r):
+    """The kernels and statistics of one time_sort result, for the JSON line."""
+    prof = r["prof"]
+    tot = max(1e-9, sum(x["total_ms"] for x in prof))
+    st = r["stats"]
+    return {"kernels": [{"name": k["name"], "launches": k["launches"], "total_ms": round(k["total_ms"], 4),
+                         "share": round(k["total_ms"] / tot, 4)}
+                        for k in sorted(prof, key=lambda k: -k["total_ms"])],
+            "profiled_ms_per_step": round(r["prof_ms"], 4),
+            "stats": {"max_bucket": st["max_bucket"], "depth": st["depth"], "repart_keys": st["repart_keys"],
+                      "split_keys": r["split_keys"]},
+            "context": {"torch_sort_ms": round(r["torch_sort_ms"], 3),
+                        "note": "torch.sort of the same keys (radix sort returning values and indices), "
+                                "not a baseline"}}
+
+
+def run_ours(a, rank, world, local):
+    import torch
+
+    torch.cuda.set_device(local)
+    r = time_sort(a, a.dtype, a.p, rank, world, local, a.steps, a.warmup, with_e2e=not a.no_e2e)
+    n = r["n"]
+    res = {"metric": "keys/s", "value": r["value"], "unit": "keys/s", "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": a.dtype, "data": "synthetic",
            "config": {"workload": workload_name(a, n), "n": n, "key": a.dtype, "dist": a.dist, "split": a.split,
                       "p": a.p, "s": a.s, "seed": a.seed, "payload": False, "det_merge": a.det_merge,
                       "l2": "inputs larger than L2 (no flush needed)", "parallelism": "replicas"},
-           "roofline": roof, "e2e": e2e, "gpu_launches": launches,
-           "clocks": clk,
-           "kernels": [{"name": k["name"], "launches": k["launches"], "total_ms": round(k["total_ms"], 4),
-                        "share": round(k["total_ms"] / max(1e-9, sum(x["total_ms"] for x in prof)), 4)}
-                       for k in sorted(prof, key=lambda k: -k["total_ms"])],
-           "stats": {"max_bucket": st["max_bucket"], "depth": st["depth"], "repart_keys": st["repart_keys"],
-                     "split_keys": split_keys},
-           "context": {"torch_sort_ms": round(torch_sort_ms, 3),
-                       "note": "torch.sort of the same keys (radix sort returning values and indices), not a baseline"}}
+           "roofline": r["roofline"], "e2e": r["e2e"], "gpu_launches": r["launches"],
+           "clocks": r["clocks"]}
+    res.update(sort_summary(a, r))
     if rank == 0 and world == 1 and not a.no_cpu:
-        res["cpu_baseline"] = cpu_baseline(a)
+        res["cpu_baseline"] = cpu_baseline(a, a.dtype, a.p)
+    # the metric's other key type: float64 keys, same n, distribution and splitter choice
+    if a.dtype == "i32" and not a.no_f64:
+        pf = a.p_f64
+        rf = time_sort(a, "f64", pf, rank, world, local, a.steps, a.warmup, with_e2e=not a.no_e2e)
+        sub = {"workload": workload_name(a, n, "f64", pf), "value": rf["value"], "unit": "keys/s",
+               "ms_per_step": rf["ms"], "dtype": "f64", "p": pf, "s": a.s, "roofline": rf["roofline"],
+               "e2e": rf["e2e"], "gpu_launches": rf["launches"], "clocks": rf["clocks"]}
+        sub.update(sort_summary(a, rf))
+        if rank == 0 and world == 1 and not a.no_cpu:
+            sub["cpu_baseline"] = cpu_baseline(a, "f64", pf, sample=min(a.cpu_sample, 1 << 22), runs=1)
+        res["f64"] = sub
     if not a.no_batched:
-        del keys, out, tk
         torch.cuda.empty_cache()
         bt = run_batched(a, rank, world, local, steps=max(3, min(a.steps, 10)), warmup=3,
                          plain_steps=a.plain_steps)
@@ -901,12 +1011,12 @@ def run_ours(a, rank, world, local):
                           "gpu_launches": bt["gpu_launches"], "graph_kernels": bt["graph_kernels"]}
     if not a.no_serving:
         torch.cuda.empty_cache()
-        count = min(a.requests, 4000)
+        count = a.requests
         sv = run_serving(a, rank, world, local, count, saturation=500)
         res["serving"] = {"workload": serving_workload_name(a, count), "value": sv["value"], "unit": "keys/s",
                           "offered": sv["offered"], "latency_ms": sv["latency_ms"], "capacity": sv["capacity"],
                           "arena_peak_gb": sv["arena_peak_gb"], "max_inflight_seen": sv["max_inflight_seen"],
-                          "gpu_launches": sv["gpu_launches"]}
+                          "gpu_launches": sv["gpu_launches"], "h2d": sv["h2d"]}
     return res
 
 
@@ -959,37 +1069,38 @@ def cpu_model():
     return platform.machine()
 
 
-def cpu_baseline(a):
-    """The oracle as it stands on the first cpu_sample keys of the same seeded
-    workload, median of three runs, single-threaded (the reported baseline); beside
-    it, on the same keys, the oracle's multi-core form (Section 2.4: steps 1 and 5
-    over every host core) and SomeSort alone (the paper's stand-alone column)."""
+def cpu_baseline(a, dtype, p, sample=None, runs=3):
+    """The oracle as it stands on the first `sample` keys of the same seeded
+    workload, median of `runs` runs, single-threaded (the reported baseline);
+    beside it, on the same keys, the oracle's multi-core form (Section 2.4: steps
+    1 and 5 over every host core) and SomeSort alone (the paper's stand-alone
+    column)."""
     import numpy as np
 
     import oracle
     from paper_1608_08648_gb300 import inputs
-    m = min(a.cpu_sample, a.keys)
-    keys = inputs.keys(a.dist, a.keys, a.dtype, seed=a.seed, p=a.p, count=m).numpy()
-    if a.dtype == "u64":
+    m = min(sample or a.cpu_sample, a.keys)
+    keys = inputs.keys(a.dist, a.keys, dtype, seed=a.seed, p=p, count=m).numpy()
+    if dtype == "u64":
         keys = keys.view(np.uint64)
     cores = cpu_cores()
 
-    def med3(fn):
+    def med(fn):
         ts = []
-        for _ in range(3):
+        for _ in range(runs):
             t0 = time.perf_counter()
             fn()
             ts.append(time.perf_counter() - t0)
         return statistics.median(ts)
 
-    t = med3(lambda: oracle.sort(keys, a.dtype, a.split, a.p, a.s, seed=a.seed))
-    t_mc = med3(lambda: oracle.sort(keys, a.dtype, a.split, a.p, a.s, seed=a.seed, threads=cores,
-                                    par_step5=True))
-    t_ss = med3(lambda: oracle.some_sort(keys, a.dtype))
+    t = med(lambda: oracle.sort(keys, dtype, a.split, p, a.s, seed=a.seed))
+    t_mc = med(lambda: oracle.sort(keys, dtype, a.split, p, a.s, seed=a.seed, threads=cores, par_step5=True))
+    t_ss = med(lambda: oracle.some_sort(keys, dtype))
+    how = f"median of {runs} oracle runs" if runs > 1 else "one oracle run"
     return {"value": m / t, "unit": "keys/s", "cores": 1, "kind": "oracle", "host_cores": cores,
             "cpu_model": cpu_model(),
-            "sample": f"first {m} keys of the same seeded workload, median of 3 oracle runs ({t:.2f} s)",
-            "multicore": {"value": m / t_mc, "unit": "keys/s", "cores": min(cores, a.p),
+            "sample": f"first {m} keys of the same seeded workload, {how} ({t:.2f} s)",
+            "multicore": {"value": m / t_mc, "unit": "keys/s", "cores": min(cores, p),
                           "kind": "oracle, multi-core form (steps 1 and 5 over the host cores)",
                           "seconds": round(t_mc, 3)},
             "some_sort_alone": {"value": m / t_ss, "unit": "keys/s", "cores": 1,

@@ -20,8 +20,10 @@
  *    keeps a small pinned status array per in-flight slot, os_sort_noalloc a
  *    static device array, and os_sort_host one copy stream per device).
  *  - Calls may come from several host threads at once, each with its own
- *    workspace: a kernel's shared-memory limit is only ever raised, so
- *    concurrent calls with different p do not interfere.
+ *    workspace.  The library's only process-wide device settings are its
+ *    kernels' shared-memory limits, each written once per device before the
+ *    kernel's first launch there, so no call changes state another call's
+ *    launches depend on.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Work is enqueued on it and the call returns without waiting, except where
  *    an entry point says it synchronizes.
@@ -182,26 +184,34 @@ int os_sort_host(int key_type, const void* h_keys_in, void* h_keys_out,
  * allocate device memory -- code inside a framework that owns all device
  * memory, or a path that must not allocate after start-up -- and so cannot
  * provide the workspace os_sort asks for.  Same arguments and semantics as
- * os_sort without d_ws, ws_bytes and stats; the workspace is a scratch array of
- * OS_NOALLOC_SCRATCH_BYTES compiled into the library, held on every device
- * where this entry point has been called until the process exits.
+ * os_sort without d_ws and ws_bytes; the workspace is a scratch array of
+ * OS_NOALLOC_SCRATCH_BYTES compiled into the library.
  *  - A sort whose os_workspace_size exceeds OS_NOALLOC_SCRATCH_BYTES is refused
  *    with OS_ERR_UNSUPPORTED before any work is enqueued (64 MiB holds, e.g.,
  *    about 8.2 million int32 keys for SqRan p = 1024, s = 16 without payload).
+ *  - The scratch is device memory of the library's module: under CUDA's default
+ *    lazy module loading it is reserved on a device when the library's kernels
+ *    are first loaded there; under eager loading (CUDA_MODULE_LOADING=EAGER) on
+ *    every device context the library touches, whether or not this entry point
+ *    is called.  Either way it stays until the process exits and counts against
+ *    the device memory other users (e.g. a serving arena) can have.
  *  - The first call on a device, with that device current, looks up the
- *    scratch's device address (cudaGetSymbolAddress); make that first call
- *    before any stream capture on the device.
+ *    scratch's device address (cudaGetSymbolAddress) and remembers it; make that
+ *    first call before any stream capture on the device.  Calls after a
+ *    cudaDeviceReset are not supported (the remembered address is stale).
  *  - All calls on a device share the scratch: calls that overlap on the GPU
  *    (on different streams without ordering) race and must be avoided.
  *    Whatever must start at zero is cleared by every call.
- *  - Device-side error flags stay in the scratch and are not reported here.
+ *  - stats: NULL (asynchronous), or filled exactly as by os_sort; then the call
+ *    synchronizes `stream` and returns OS_ERR_DEVICE if a kernel flagged an
+ *    error in the status word (a skipped access or a bucket left too large).
  * Calls no allocating routine.
  */
 #define OS_NOALLOC_SCRATCH_BYTES (64u << 20)
 
 int os_sort_noalloc(int key_type, const void* d_keys_in, void* d_keys_out,
                     const uint32_t* d_vals_in, uint32_t* d_vals_out, uint64_t n,
-                    const os_params* prm, void* stream);
+                    const os_params* prm, void* stream, os_stats* stats);
 
 /*
  * ---- Batched segmented sort -------------------------------------------------
@@ -369,10 +379,17 @@ typedef struct {
     uint32_t max_inflight;  /* admitted, unfinished requests at most, >= 1 */
 } os_server_config;
 
+/* Flags of os_request.flags. */
+#define OS_REQ_HOST_INPUT 1u   /* d_keys_in is HOST memory (pinned for full copy speed): the server copies
+                                  the keys into the request's output block on the request's stream when it
+                                  admits the request, then sorts them there in place; the copy counts in the
+                                  request's latency.  The host keys are read until the request is done. */
+
 typedef struct {
     int32_t     key_type;
-    uint32_t    reserved;   /* must be 0 */
-    const void* d_keys_in;  /* n device keys, resident, outside the arena; read until the request is done */
+    uint32_t    flags;      /* 0 or OS_REQ_HOST_INPUT */
+    const void* d_keys_in;  /* n keys, resident on the device outside the arena (or on the host with
+                               OS_REQ_HOST_INPUT); read until the request is done */
     uint64_t    n;
     os_params   prm;
 } os_request;

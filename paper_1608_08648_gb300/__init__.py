@@ -29,6 +29,13 @@ class OssortError(RuntimeError):
         self.status = status
 
 
+def _key_type_host(t, key_type):
+    import torch
+    if key_type is not None:
+        return KEY_TYPES[key_type] if isinstance(key_type, str) else int(key_type)
+    return {torch.int32: OS_I32, torch.float64: OS_F64, torch.int64: OS_U64}[t.dtype]
+
+
 def _key_type(t, key_type):
     import torch
     if key_type is not None:
@@ -273,11 +280,14 @@ class Server:
         self._inputs = {}      # ticket -> (input tensor, dtype): kept alive while the request may read it
 
     def request(self, keys, split="ran", p=1024, s=16, seed=0, key_type=None):
-        kt = _key_type(keys, key_type)
-        return self._b.os_request(kt, 0, keys.data_ptr(), keys.numel(), params(split, p, s, seed))
+        """An os_request for keys resident on the device, or (a CPU tensor, best
+        pinned) keys the server copies in itself when it admits the request."""
+        kt = _key_type(keys, key_type) if keys.is_cuda else _key_type_host(keys, key_type)
+        flags = 0 if keys.is_cuda else self._b.OS_REQ_HOST_INPUT
+        return self._b.os_request(kt, flags, keys.data_ptr(), keys.numel(), params(split, p, s, seed))
 
     def submit(self, keys, split="ran", p=1024, s=16, seed=0, key_type=None):
-        assert keys.is_cuda and keys.dim() == 1 and keys.is_contiguous()
+        assert keys.dim() == 1 and keys.is_contiguous()
         rc, t = self._b.os_server_submit(self.handle, self.request(keys, split, p, s, seed, key_type))
         if rc != OS_OK:
             raise OssortError(rc, "os_server_submit")

@@ -15,6 +15,7 @@ OS_I32, OS_U64, OS_F64, OS_S32 = 0, 1, 2, 3
 OS_DET, OS_RAN = 0, 1
 OS_OK, OS_ERR_ARG, OS_ERR_WS, OS_ERR_UNSUPPORTED, OS_ERR_CUDA, OS_ERR_DEVICE = range(6)
 OS_STABLE = 1
+OS_REQ_HOST_INPUT = 1
 OS_DET_MERGE = 2
 OS_MAX_N = 1 << 31
 OS_MAX_P = 4096
@@ -60,7 +61,7 @@ class os_server_config(ctypes.Structure):
 
 
 class os_request(ctypes.Structure):
-    _fields_ = [("key_type", _i32), ("reserved", _u32), ("d_keys_in", _vp), ("n", _u64), ("prm", os_params)]
+    _fields_ = [("key_type", _i32), ("flags", _u32), ("d_keys_in", _vp), ("n", _u64), ("prm", os_params)]
 
 
 class os_result(ctypes.Structure):
@@ -109,7 +110,8 @@ def lib() -> ctypes.CDLL:
         L.os_sort_host.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp, _u64, ctypes.POINTER(os_params), _vp, _sz,
                                    _vp]
         L.os_sort_noalloc.restype = ctypes.c_int
-        L.os_sort_noalloc.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp, _u64, ctypes.POINTER(os_params), _vp]
+        L.os_sort_noalloc.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp, _u64, ctypes.POINTER(os_params), _vp,
+                                      ctypes.POINTER(os_stats)]
         L.os_launch_count.restype = _u64
         L.os_launch_count.argtypes = []
         L.os_profile_start.restype = ctypes.c_int
@@ -198,9 +200,10 @@ def os_sort_host(key_type: int, h_keys_in: int, h_keys_out: int, h_vals_in: int 
 
 
 def os_sort_noalloc(key_type: int, d_keys_in: int, d_keys_out: int, d_vals_in: int | None,
-                    d_vals_out: int | None, n: int, prm: os_params, stream: int | None) -> int:
+                    d_vals_out: int | None, n: int, prm: os_params, stream: int | None,
+                    stats: "os_stats | None" = None) -> int:
     return lib().os_sort_noalloc(key_type, d_keys_in, d_keys_out, d_vals_in, d_vals_out, n, ctypes.byref(prm),
-                                 stream)
+                                 stream, ctypes.byref(stats) if stats is not None else None)
 
 
 def os_check(d_ws: int, stream: int | None) -> tuple[int, int]:

@@ -51,19 +51,33 @@ inline unsigned grid_for(uint64_t work, int threads, unsigned cap = 4096) {
 
 constexpr uint32_t G_CAP = 2048;   // most CTAs of the grid-wide classify / scatter
 
-// Raise a kernel's dynamic shared-memory limit to at least `bytes`, never lower
-// it.  The limit belongs to the kernel, not to a call: sorts running at once on
-// other host threads with other p would otherwise set it back below what a launch
-// of this one, already queued, needs.  One limit per (device, kernel), under a lock.
+// A kernel's dynamic shared-memory limit (cudaFuncAttributeMaxDynamicSharedMemorySize)
+// is process-wide state of the kernel, shared by every host thread.  It is
+// written exactly once per (device, kernel), to the most the device allows that
+// kernel (the opt-in maximum less its static shared memory), by the first call
+// that needs the kernel, under a lock, and before that call launches it.  Every
+// launch of the kernel, on any thread, comes after its own call here, so no
+// attribute write can overlap a launch of the same kernel on another thread and
+// no later call ever changes a limit a queued launch was checked against.  The
+// limit is only a ceiling: the shared memory a launch gets is the size it asks
+// for, so occupancy and grid sizes are unchanged by it.
 inline void smem_at_least(const void* fn, size_t bytes) {
     static std::mutex mu;
     static std::map<std::pair<int, const void*>, size_t> cur;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return;
     std::lock_guard<std::mutex> lock(mu);
-    size_t& c = cur[{dev, fn}];
-    if (bytes > c && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
-        c = bytes;
+    auto it = cur.find({dev, fn});
+    if (it != cur.end()) return;   // set once; a launch above the limit fails with a launch error
+    int optin = 0;
+    cudaFuncAttributes fa{};
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, fn) != cudaSuccess)
+        return;
+    const size_t most = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    (void)bytes;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most) == cudaSuccess)
+        cur[{dev, fn}] = most;
 }
 
 template <class K>

@@ -135,8 +135,18 @@ void dispatch_loop(os_server_s* s) {
         cudaStream_t st = s->streams[best];
         char* out = s->arena + off;
         char* ws = out + q->out_bytes;
-        const int rc = os_sort(q->r.key_type, q->r.d_keys_in, out, nullptr, nullptr, q->r.n, &q->r.prm, ws,
-                               q->ws_bytes, st, nullptr);
+        int rc = OS_OK;
+        const void* kin = q->r.d_keys_in;
+        if ((q->r.flags & OS_REQ_HOST_INPUT) && q->r.n > 0) {
+            // host keys: copied into the output block, then sorted there in place
+            const cudaError_t ce = cudaMemcpyAsync(out, kin, q->r.n * key_bytes_of(q->r.key_type),
+                                                   cudaMemcpyHostToDevice, st);
+            if (ce != cudaSuccess) rc = cuda_fail(ce);
+            kin = out;
+        }
+        if (rc == OS_OK)
+            rc = os_sort(q->r.key_type, kin, out, nullptr, nullptr, q->r.n, &q->r.prm, ws, q->ws_bytes, st,
+                         nullptr);
         uint32_t* hs = s->h_status + q->slot * STATUS_WORDS;
         hs[0] = 0;
         q->status = rc;   // written before the callback is enqueued
@@ -155,7 +165,7 @@ void dispatch_loop(os_server_s* s) {
 }
 
 int check_request(const os_request* req, size_t& ws_bytes) {
-    if (!req || req->reserved != 0) return OS_ERR_ARG;
+    if (!req || (req->flags & ~OS_REQ_HOST_INPUT) != 0) return OS_ERR_ARG;
     if (req->key_type == OS_S32) return OS_ERR_UNSUPPORTED;   // its sort synchronizes its stream
     if (req->n > 0 && !req->d_keys_in) return OS_ERR_ARG;
     return os_workspace_size(req->key_type, req->n, 0, &req->prm, &ws_bytes);

@@ -156,3 +156,30 @@ def test_concurrent_host_threads_with_different_p():
     for t in threads:
         t.join()
     assert not wrong, f"wrong results (p, repetition): {wrong[:8]}"
+
+
+def test_host_input_requests_match_solo_sorts():
+    # requests whose keys are in pinned host memory: the server copies them in
+    # after admission; every result equals the device-resident solo sort
+    trace = inputs.serving_trace(24, lo=4096, hi=1 << 20, seed=9)
+    src = sources(1 << 20, seed=9)
+    hsrc = {k: v.cpu().pin_memory() for k, v in src.items()}
+    with oss.Server(2 << 30, streams=4, max_inflight=8) as srv:
+        bad = B.os_request(B.OS_I32, 2, hsrc[("i32", "uniform")].data_ptr(), 16, oss.params("ran", 4, 4, 0))
+        assert B.os_server_submit(srv.handle, bad)[0] == B.OS_ERR_ARG      # unknown request flag
+        tickets = {}
+        for i in range(24):
+            dt, dist, n, off = trace["dtype"][i], trace["dist"][i], trace["n"][i], trace["offset"][i]
+            tickets[srv.submit(hsrc[(dt, dist)][off:off + n], seed=trace["req_seed"][i], key_type=dt)] = i
+        got = 0
+        while got < 24:
+            for t, status, out, rec in srv.poll(timeout_us=200_000):
+                assert status == B.OS_OK
+                i = tickets[t]
+                dt, keys = trace_inputs(trace, src, i)
+                ref = alone(keys, dt, trace["req_seed"][i])
+                torch.cuda.synchronize()
+                assert torch.equal(as_int(out), as_int(ref)), f"host-input request {i} differs from its solo sort"
+                srv.release(t)
+                got += 1
+        assert srv.stats()["arena_in_use"] == 0

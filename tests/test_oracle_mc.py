@@ -55,8 +55,11 @@ def test_bench_cpu_baseline_fields():
     import bench
     a = argparse.Namespace(cpu_sample=1 << 14, keys=1 << 20, dist="uniform", dtype="i32", seed=1, p=16, s=4,
                            split="ran")
-    cb = bench.cpu_baseline(a)
+    cb = bench.cpu_baseline(a, "i32", 16)
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] > 0
+    assert "median of 3" in cb["sample"]
+    one = bench.cpu_baseline(a, "f64", 16, sample=1 << 12, runs=1)
+    assert one["value"] > 0 and "one oracle run" in one["sample"] and "4096 keys" in one["sample"]
     assert cb["multicore"]["value"] > 0 and cb["multicore"]["cores"] >= 1
     assert cb["some_sort_alone"]["value"] > 0
     assert isinstance(cb["cpu_model"], str) and cb["cpu_model"]

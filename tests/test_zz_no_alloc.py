@@ -32,13 +32,19 @@ def _reference_sort(keys, vals, prm, kt):
     return out, vout
 
 
-def _noalloc_sort(keys, vals, prm, kt):
+def _noalloc_sort(keys, vals, prm, kt, with_stats=False):
     n = keys.numel()
     out = torch.empty_like(keys)
     vout = torch.empty_like(vals) if vals is not None else None
     st = torch.cuda.current_stream().cuda_stream
+    stats = None
+    if with_stats:
+        # host arrays left NULL: only the counters and the device status word
+        stats = B.os_stats(0, 0, 0, 0, None, None, None)
     rc = B.os_sort_noalloc(kt, keys.data_ptr(), out.data_ptr(), vals.data_ptr() if vals is not None else None,
-                           vout.data_ptr() if vout is not None else None, n, prm, st)
+                           vout.data_ptr() if vout is not None else None, n, prm, st, stats)
+    # with statistics the call synchronizes and returns OS_ERR_DEVICE if any
+    # kernel flagged an error bit in the scratch's status word
     assert rc == B.OS_OK, B.os_strerror(rc)
     return out, vout
 
@@ -55,8 +61,8 @@ def test_noalloc_matches_os_sort_on_two_calls_in_a_row():
         keys = inputs.keys("uniform", n, kt_name, seed=seed, p=p, device="cuda")
         vals = torch.arange(n, dtype=torch.int32, device="cuda") if with_vals else None
         ref_k, ref_v = _reference_sort(keys, vals, prm, kt)
-        for _ in range(2):          # the scratch keeps the previous call's contents
-            got_k, got_v = _noalloc_sort(keys, vals, prm, kt)
+        for rep in range(2):        # the scratch keeps the previous call's contents
+            got_k, got_v = _noalloc_sort(keys, vals, prm, kt, with_stats=(rep == 1))
             torch.cuda.synchronize()
             assert torch.equal(got_k, ref_k)
             if with_vals:
@@ -65,7 +71,7 @@ def test_noalloc_matches_os_sort_on_two_calls_in_a_row():
     keys2 = inputs.keys("dup", 777_777, "i32", seed=5, device="cuda")
     prm2 = oss.params("ran", 256, 8, 5)
     ref2, _ = _reference_sort(keys2, None, prm2, B.OS_I32)
-    got2, _ = _noalloc_sort(keys2, None, prm2, B.OS_I32)
+    got2, _ = _noalloc_sort(keys2, None, prm2, B.OS_I32, with_stats=True)
     torch.cuda.synchronize()
     assert torch.equal(got2, ref2)
     assert torch.equal(got2, torch.sort(keys2).values)
