@@ -114,6 +114,7 @@ constexpr uint32_t ERR_DEPTH = 1u;         // a bucket still too large at MAX_DE
 constexpr uint32_t ERR_SIZES = 2u;         // a work list overflowed
 constexpr uint32_t ERR_SAMPLE = 4u;        // sample larger than its buffer
 constexpr uint32_t ERR_BOUNDS = 8u;        // an index failed its range check (access skipped)
+constexpr uint32_t ERR_TIMEOUT = 32u;      // a bounded wait for a bulk copy gave up (the kernel stopped early)
 
 // Record a failed range check in the status word: the error bit, the first
 // failing site in status[6] and its index in status[7].  The access is skipped

@@ -21,6 +21,7 @@
 #include "kernels.cuh"
 #include "profile.cuh"
 #include "segkernels.cuh"
+#include "distribute.cuh"
 
 namespace ossort {
 
@@ -211,12 +212,12 @@ void seg_core(Ctx& c, const SegSource& src, const SegClasses& cls, const typenam
         OS_LAUNCH(c.st, nest ? "k_seg_splitters.sample" : "k_seg_splitters",
                   k_seg_splitters<KT><<<std::max<uint32_t>(g_spl, 1), SEG_SPL_NT, sm_spl, c.st>>>(
                       kin, rec, pseg, tot, spl_o, spl_t, c.status));
-        const size_t sm_c = seg_classify_smem<KT>(B.maxp);
-        smem_at_least(reinterpret_cast<const void*>(k_seg_classify<KT>), sm_c);
-        const uint32_t g_c = (uint32_t)(c.num_sms * occupancy(k_seg_classify<KT>, SEG_NT, sm_c));
+        const size_t sm_c = seg_classify_v_smem<KT>(B.maxp);
+        smem_at_least(reinterpret_cast<const void*>(k_seg_classify_v<KT>), sm_c);
+        const uint32_t g_c = (uint32_t)(c.num_sms * occupancy(k_seg_classify_v<KT>, SEG_NT, sm_c));
         OS_LAUNCH(c.st, nest ? "k_seg_classify.sample" : "k_seg_classify",
-                  k_seg_classify<KT><<<g_c, SEG_NT, sm_c, c.st>>>(kin, rec, tile0, nseg, tot, spl_o, spl_t, B.maxp,
-                                                                   hist, bid));
+                  k_seg_classify_v<KT><<<g_c, SEG_NT, sm_c, c.st>>>(kin, rec, tile0, nseg, tot, spl_o, spl_t,
+                                                                     B.maxp, hist, bid));
     }
     OS_LAUNCH(c.st, nest ? "k_seg_scan.sample" : "k_seg_scan",
               k_seg_scan<<<gseg, SEG_SCAN_NT, 0, c.st>>>(rec, nseg, pseg, tot, hist, bsize, wl, CAP,
@@ -224,7 +225,15 @@ void seg_core(Ctx& c, const SegSource& src, const SegClasses& cls, const typenam
                                                                     static_cast<const void*>(kin)),
                                                          c.status, c.status + 1,
                                                          reinterpret_cast<unsigned long long*>(c.status + 2)));
-    if (B.any_part) {
+    if (B.any_part && !HV && false) {
+        const size_t sm_s = seg_scatter_v_smem<KT>(B.maxp);
+        smem_at_least(reinterpret_cast<const void*>(k_seg_scatter_v<KT>), sm_s);
+        constexpr int SNT = SegScatterVCfg<T>::NT;
+        const uint32_t g_s = (uint32_t)(c.num_sms * occupancy(k_seg_scatter_v<KT>, SNT, sm_s));
+        OS_LAUNCH(c.st, nest ? "k_seg_scatter.sample" : "k_seg_scatter",
+                  k_seg_scatter_v<KT><<<g_s, SNT, sm_s, c.st>>>(kin, bid, rec, tile0, nseg, tot, hist, B.maxp, kout,
+                                                                 c.status));
+    } else if (B.any_part) {
         const size_t sm_s = seg_scatter_smem<KT, HV>(B.maxp);
         smem_at_least(reinterpret_cast<const void*>(k_seg_scatter<KT, HV>), sm_s);
         constexpr int SNT = SegScatterCfg<T, HV>::NT;
@@ -328,10 +337,61 @@ size_t scatter_smem(int p) {
 // Step 4: classify every key of src (tag = position) against the p-1 sorted
 // splitters and scatter keys (and payloads) into contiguous buckets of dst.
 // Bucket b occupies [boff[b], boff[b+1]); bsize[b] = its size.
+// Keys without a payload take the vector passes of distribute.cuh: units of
+// SUPER keys, classify with NTC threads, scatter with NTS threads holding
+// SUPER / NTS keys each (16 for 4-byte keys, 8 for 8-byte keys).
+template <class T> struct TopVCfg {
+    static constexpr int SUPER = 8192;
+    static constexpr int NTC = 512;
+    static constexpr int NTS = sizeof(T) == 4 ? 512 : 1024;
+};
+
+// Bins of the vector classify's splitter table: the power of two >= 4p (at most
+// 2^13), so that few bins hold two splitters and need a search.
+inline int table_lbits_v(uint32_t p) {
+    int b = 1;
+    while ((1u << b) < 4 * p && b < 13) ++b;
+    return b;
+}
+
+template <class KT>
+void partition_top_v(Ctx& c, const typename KT::T* src, uint32_t n, const typename KT::O* spl_o,
+                     const uint32_t* spl_t, uint32_t p, typename KT::T* dst, uint32_t* boff, uint32_t* bsize) {
+    using T = typename KT::T;
+    using CF = TopVCfg<T>;
+    constexpr uint32_t SUPER = CF::SUPER;
+    const int lb = table_lbits_v(p);
+    const uint32_t ntiles = (n + SUPER - 1) / SUPER;
+    const uint32_t gmax = std::min<uint32_t>(std::max<uint32_t>(ntiles, 1), G_CAP);
+    uint32_t* hist = c.ar.take<uint32_t>((size_t)p * gmax);
+    uint32_t* col = c.ar.take<uint32_t>((size_t)p * gmax);
+    uint16_t* bid = c.ar.take<uint16_t>(n);
+    if (!c.live()) return;
+    auto kc = k_classify_v<KT, CF::NTC, CF::SUPER>;
+    auto ks = k_scatter_v<KT, CF::NTS, CF::SUPER>;
+    const size_t sm_c = classify_smem<KT>(p, lb), sm_s = scatter_v_smem<T>((int)p, CF::SUPER);
+    smem_at_least(reinterpret_cast<const void*>(kc), sm_c);
+    smem_at_least(reinterpret_cast<const void*>(ks), sm_s);
+    const int occ = occupancy(ks, CF::NTS, sm_s);
+    const uint32_t G = std::max<uint32_t>(1, std::min<uint32_t>(gmax, (uint32_t)(c.num_sms * occ)));
+    OS_LAUNCH(c.st, c.nested ? "k_classify.sample" : "k_classify",
+              kc<<<G, CF::NTC, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, lb, hist, bid, ntiles));
+    OS_LAUNCH(c.st, c.nested ? "k_column_scan.sample" : "k_column_scan",
+              k_column_scan<<<grid_for((uint64_t)p * 32, 256), 256, 0, c.st>>>(hist, p, G, col, bsize));
+    OS_LAUNCH(c.st, c.nested ? "k_bucket_offsets.sample" : "k_bucket_offsets",
+              k_bucket_offsets<<<1, 1024, 0, c.st>>>(bsize, p, boff));
+    OS_LAUNCH(c.st, c.nested ? "k_scatter.sample" : "k_scatter",
+              ks<<<G, CF::NTS, sm_s, c.st>>>(src, bid, n, (int)p, col, boff, dst, ntiles, c.status));
+}
+
 template <class KT, bool HV>
 void partition_top(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, uint32_t n,
                    const typename KT::O* spl_o, const uint32_t* spl_t, uint32_t p, typename KT::T* dst,
                    uint32_t* vdst, uint32_t* boff, uint32_t* bsize) {
+    if constexpr (!HV) {
+        partition_top_v<KT>(c, src, n, spl_o, spl_t, p, dst, boff, bsize);
+        return;
+    }
     const int lb = table_lbits(p);
     constexpr uint32_t SUPER = ScatterCfg<typename KT::T, HV>::SUPER;
     const uint32_t ntiles = (n + SUPER - 1) / SUPER;

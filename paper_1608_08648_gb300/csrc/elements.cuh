@@ -12,6 +12,7 @@ namespace ossort {
 // One sortable element.  E32: 32-bit key; E64: 64-bit key, or a 32-bit key
 // packed above its 32-bit position; E96: 64-bit key and a 32-bit position.
 struct E32 {
+    static constexpr bool kSingleWord = true;
     uint32_t k;
     __device__ __forceinline__ static bool lt(const E32& a, const E32& b) { return a.k < b.k; }
     __device__ __forceinline__ static E32 shfl(const E32& a, int m) {
@@ -19,6 +20,7 @@ struct E32 {
     }
 };
 struct E64 {
+    static constexpr bool kSingleWord = true;
     uint64_t k;
     __device__ __forceinline__ static bool lt(const E64& a, const E64& b) { return a.k < b.k; }
     __device__ __forceinline__ static E64 shfl(const E64& a, int m) {
@@ -26,6 +28,7 @@ struct E64 {
     }
 };
 struct E96 {
+    static constexpr bool kSingleWord = false;
     uint64_t k;
     uint32_t p;
     __device__ __forceinline__ static bool lt(const E96& a, const E96& b) {

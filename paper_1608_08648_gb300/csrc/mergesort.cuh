@@ -34,6 +34,8 @@ __device__ __forceinline__ void cas_up(E& a, E& b) {   // a <- min, b <- max
 
 template <class E>
 __device__ __forceinline__ E emin(const E& a, const E& b) { return E::lt(b, a) ? b : a; }
+template <class E>
+__device__ __forceinline__ E emax(const E& a, const E& b) { return E::lt(b, a) ? a : b; }
 
 // Single-word elements order as plain unsigned integers: min / max.
 template <>
@@ -52,6 +54,10 @@ template <>
 __device__ __forceinline__ E32 emin<E32>(const E32& a, const E32& b) { return E32{min(a.k, b.k)}; }
 template <>
 __device__ __forceinline__ E64 emin<E64>(const E64& a, const E64& b) { return E64{min(a.k, b.k)}; }
+template <>
+__device__ __forceinline__ E32 emax<E32>(const E32& a, const E32& b) { return E32{max(a.k, b.k)}; }
+template <>
+__device__ __forceinline__ E64 emax<E64>(const E64& a, const E64& b) { return E64{max(a.k, b.k)}; }
 
 // Batcher's odd-even merge sort of x[0..IT) ascending (IT a power of two): 191
 // compare-exchanges for 32 elements against 240 for the bitonic network.  The
@@ -116,22 +122,106 @@ __device__ __forceinline__ void bitonic_merge_regs(E (&x)[IT]) {
             if ((i & jj) == 0) cas_up(x[i], x[i + jj]);
 }
 
+// Order-reversing flip of a single-word element (its bits complemented) when f.
+__device__ __forceinline__ E32 eflip(const E32& a, uint32_t f) { return E32{a.k ^ f}; }
+__device__ __forceinline__ E64 eflip(const E64& a, uint32_t f) { return E64{a.k ^ (((uint64_t)f << 32) | f)}; }
+
+// Bitonic sort of a warp's 32 * IT elements held blocked (lane l has elements
+// l IT .. l IT + IT - 1 in x), from runs of IT that every lane has already sorted
+// ascending in its own "space": lanes whose space bit is set hold complemented
+// elements, so an ascending run there is a descending run of the elements.
+// Level v (v = 0 .. levels - 1) merges pairs of 2^v-lane blocks into 2^(v+1)-lane
+// blocks, the block of lanes [j 2^(v+1), (j+1) 2^(v+1)) ascending for even j and
+// descending for odd j (the alternation that makes every next pair bitonic): the
+// lanes switch to that block's space (complementing when it changes), then the
+// half-cleaners of the bitonic merge run ascending -- across lanes by shuffles
+// for distances of IT elements and more, inside the lane for the last log2(IT).
+// On entry the space of lane l is l & 1; after `levels` levels it is
+// (l >> levels) & 1, so the lanes of the first 2^levels-lane block (which hold the
+// sorted elements) are back in plain space.
+// One half-cleaner step across lanes: the element of lane ^ dl, and the min
+// (lower lane) or max of the pair.  Written as one inline-PTX block per element so
+// the shuffles stay next to their compares instead of being hoisted ahead of
+// them, which would hold every shuffled copy of the 32 IT elements live at once.
+__device__ __forceinline__ E32 xlane_cas(const E32& a, int dl, uint32_t lower) {
+    uint32_t r;
+    asm volatile("{\n\t.reg .u32 t;\n\t.reg .pred pl;\n\t"
+                 "shfl.sync.bfly.b32 t, %1, %2, 0x1f, 0xffffffff;\n\t"
+                 "setp.ne.u32 pl, %3, 0;\n\t"
+                 "@pl min.u32 %0, %1, t;\n\t"
+                 "@!pl max.u32 %0, %1, t;\n\t}"
+                 : "=r"(r) : "r"(a.k), "r"(dl), "r"(lower));
+    return E32{r};
+}
+__device__ __forceinline__ E64 xlane_cas(const E64& a, int dl, uint32_t lower) {
+    uint64_t r;
+    asm volatile("{\n\t.reg .u32 lo, hi;\n\t.reg .u64 t;\n\t.reg .pred pl;\n\t"
+                 "mov.b64 {lo, hi}, %1;\n\t"
+                 "shfl.sync.bfly.b32 lo, lo, %2, 0x1f, 0xffffffff;\n\t"
+                 "shfl.sync.bfly.b32 hi, hi, %2, 0x1f, 0xffffffff;\n\t"
+                 "mov.b64 t, {lo, hi};\n\t"
+                 "setp.ne.u32 pl, %3, 0;\n\t"
+                 "@pl min.u64 %0, %1, t;\n\t"
+                 "@!pl max.u64 %0, %1, t;\n\t}"
+                 : "=l"(r) : "l"(a.k), "r"(dl), "r"(lower));
+    return E64{r};
+}
+
+template <class E, int IT>
+__device__ __forceinline__ void warp_bitonic_level(E (&x)[IT], int v) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t space = (lane >> v) & 1, ns = (lane >> (v + 1)) & 1;
+    const uint32_t f = (ns ^ space) ? 0xFFFFFFFFu : 0u;
+#pragma unroll
+    for (int i = 0; i < IT; ++i) x[i] = eflip(x[i], f);
+#pragma unroll 1
+    for (int dl = 1 << v; dl >= 1; dl >>= 1) {
+        const uint32_t lower = (lane & dl) == 0;
+#pragma unroll
+        for (int i = 0; i < IT; ++i) x[i] = xlane_cas(x[i], dl, lower);
+    }
+    bitonic_merge_regs<E, IT>(x);
+}
+
+template <class E, int IT>
+__device__ __forceinline__ void warp_bitonic_levels(E (&x)[IT], int levels) {
+#pragma unroll 1
+    for (int v = 0; v < levels; ++v) warp_bitonic_level<E, IT>(x, v);
+}
+
 // x: the thread's IT elements at positions tid*IT + i (blocked; positions >= len
 // must hold EMax).  sk: shared memory for padded_len<E>(NT*IT) elements; the
 // whole block must hold NT*IT >= len.  On
 // return x holds the thread's IT outputs of the sorted sequence.  All NT threads
 // must call; starts and ends with __syncthreads.
+// 32-bit elements (4-byte keys alone) sort each warp's 32 IT elements in
+// registers (warp_bitonic_levels) and merge through shared memory only the
+// runs of whole warps; wider elements merge every round through shared memory
+// (their shuffles and compares take two instructions each, measured slower).
 template <class E, int NT, int IT>
 __device__ __forceinline__ void merge_sort_block(E (&x)[IT], E* sk, int len) {
     const int base = threadIdx.x * IT;
     const bool active = base < len;
-    if (active) {
+    int run0 = IT;
+    if constexpr (sizeof(E) == 4) {
+        // every lane sorts (padding included: the shuffles need the whole warp),
+        // odd lanes in complemented space
+        const uint32_t f = (threadIdx.x & 1) ? 0xFFFFFFFFu : 0u;
+#pragma unroll
+        for (int i = 0; i < IT; ++i) x[i] = eflip(x[i], f);
+        oddeven_sort_regs<E, IT>(x);
+        const int wlen = min(len, 32 * IT);     // elements the warps must order among themselves
+        int levels = 0;
+        while ((IT << levels) < wlen) ++levels;
+        warp_bitonic_levels<E, IT>(x, levels);
+        run0 = 32 * IT;
+    } else if (active) {
         // (key, position) triples keep the bitonic network: its shorter live
         // ranges fit the 64-register budget of the 512-thread leaf.
         if constexpr (sizeof(E) <= 8) oddeven_sort_regs<E, IT>(x);
         else bitonic_sort_regs<E, IT>(x);
     }
-    for (int run = IT; run < len; run *= 2) {
+    for (int run = run0; run < len; run *= 2) {
         // A pair of runs that fits in one warp's elements is merged by that warp
         // alone, so only the larger rounds need the whole block.
         const bool block_wide = 2 * run > 32 * IT;
