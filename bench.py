@@ -907,6 +907,9 @@ def time_sort(a, dtype, p, rank, world, local, steps, warmup, with_e2e=True):
         t = max_over_ranks(t, world)
         # the device sort of the same keys (out) is the reference for the host result
         assert torch.equal(h_out, out.cpu()), "e2e output differs from the device-resident sort"
+        del h_in, h_out
+        if hasattr(torch._C, "_host_emptyCache"):
+            torch._C._host_emptyCache()      # return the pinned buffers to the host before the next leg
         e2e = {"value": world * n / t, "unit": "keys/s", "ms_per_step": t * 1e3,
                "h2d_bytes_per_step": n * kb, "d2h_bytes_per_step": n * kb,
                "host_link_gbs": {"h2d": link[0], "d2h": link[1],

@@ -220,8 +220,8 @@ __host__ __device__ constexpr size_t scatter_v_smem(int p, int super) {
 template <class KT, int NT, int SUPER>
 __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : (NT >= 512 ? 2 : 4))
 k_scatter_v(const typename KT::T* __restrict__ keys, const uint16_t* __restrict__ bid, uint32_t n, int p,
-            const uint32_t* __restrict__ col, const uint32_t* __restrict__ boff, typename KT::T* __restrict__ out,
-            uint32_t ntiles, uint32_t* status) {
+            const uint32_t* __restrict__ col, uint32_t cstep, const uint32_t* __restrict__ boff,
+            typename KT::T* __restrict__ out, uint32_t ntiles, uint32_t* status) {
     using T = typename KT::T;
     constexpr int VEC = VecOf<T>::N;
     constexpr int NV = SUPER / (NT * VEC);           // vectors per thread per unit
@@ -237,8 +237,11 @@ k_scatter_v(const typename KT::T* __restrict__ keys, const uint16_t* __restrict_
     uint32_t* scratch = reinterpret_cast<uint32_t*>(q);  q += sizeof(uint32_t) * 32;   // one word per warp
     uint32_t* stop = reinterpret_cast<uint32_t*>(q);
 
+    // the classify ran with cstep CTAs per scatter CTA (its CTAs 2g, 2g+1 for
+    // cstep = 2 cover exactly this CTA's units): col has G * cstep columns and
+    // this CTA's keys of bucket b start at column g * cstep
     const uint32_t G = gridDim.x, g = blockIdx.x;
-    for (int b = threadIdx.x; b < p; b += NT) cursor[b] = boff[b] + col[(size_t)b * G + g];
+    for (int b = threadIdx.x; b < p; b += NT) cursor[b] = boff[b] + col[((size_t)b * G + g) * cstep];
     const uint32_t t0 = tile_lo(g, G, ntiles), t1 = tile_lo(g + 1, G, ntiles);
     const bool vec_ok = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
     auto whole = [&](uint32_t t) { return (uint64_t)(t + 1) * SUPER <= n; };
@@ -497,140 +500,6 @@ k_seg_classify_v(const typename KT::T* __restrict__ keys, const SegRec* __restri
         __syncthreads();
         for (int b = threadIdx.x; b < p; b += SEG_NT) hist[r.hist0 + (size_t)b * r.ntile + tl] = cnt[b];
         __syncthreads();
-    }
-}
-
-// Scatter of keys without a payload in the bucket phase: per tile, sub-tiles
-// of NTS * NV vector slots, ranked by shared-memory counters, staged by bucket
-// and written out as runs (the scheme of k_scatter_v).
-template <class T> struct SegScatterVCfg {
-    static constexpr int NT = 256;
-    static constexpr int NV = 4;                                   // vector slots per thread per sub-tile
-    static constexpr int SUB = NT * NV * VecOf<T>::N;              // keys staged at most per sub-tile
-};
-
-template <class KT>
-size_t seg_scatter_v_smem(int maxp) {
-    using T = typename KT::T;
-    constexpr int SUB = SegScatterVCfg<T>::SUB;
-    return sizeof(T) * SUB + sizeof(uint16_t) * SUB + sizeof(uint32_t) * (size_t)(3 * maxp + 2) +
-           sizeof(uint32_t) * 32 + 64;
-}
-
-template <class KT>
-__global__ void __launch_bounds__(SegScatterVCfg<typename KT::T>::NT, 3)
-k_seg_scatter_v(const typename KT::T* __restrict__ keys, const uint16_t* __restrict__ bid,
-                const SegRec* __restrict__ rec, const uint32_t* __restrict__ tile0, uint32_t nseg,
-                const SegTotals* __restrict__ tot, const uint32_t* __restrict__ col, int maxp,
-                typename KT::T* __restrict__ out, uint32_t* status) {
-    using T = typename KT::T;
-    using CF = SegScatterVCfg<T>;
-    constexpr int VEC = VecOf<T>::N, NT = CF::NT, NV = CF::NV, SUB = CF::SUB;
-    extern __shared__ __align__(16) char smem[];
-    char* q = smem;
-    T* sk = reinterpret_cast<T*>(q);                     q += sizeof(T) * SUB;
-    uint16_t* sb = reinterpret_cast<uint16_t*>(q);       q += sizeof(uint16_t) * SUB;
-    uint32_t* toff = reinterpret_cast<uint32_t*>(q);     q += sizeof(uint32_t) * (maxp + 1);
-    uint32_t* cursor = reinterpret_cast<uint32_t*>(q);   q += sizeof(uint32_t) * maxp;
-    int32_t* delta = reinterpret_cast<int32_t*>(q);      q += sizeof(uint32_t) * (maxp + 1);
-    uint32_t* scratch = reinterpret_cast<uint32_t*>(q);
-
-    const uint32_t T_ = tot->tiles;
-    const uint32_t t0 = tile_lo(blockIdx.x, gridDim.x, T_), t1 = tile_lo(blockIdx.x + 1, gridDim.x, T_);
-    const bool vec_ok = (reinterpret_cast<uintptr_t>(keys) & 15) == 0 &&
-                        (reinterpret_cast<uintptr_t>(bid) & 7) == 0;
-    SegRec r{};
-    uint32_t seg_t0 = 0, seg_t1 = 0;
-    for (uint32_t t = t0; t < t1; ++t) {
-        if (t >= seg_t1 || t < seg_t0) {
-            const uint32_t g = seg_of_tile(tile0, nseg, t);
-            r = rec[g];
-            seg_t0 = tile0[g];
-            seg_t1 = tile0[g + 1];
-        }
-        const int p = (int)r.p;
-        const uint32_t tl = t - seg_t0;
-        const uint32_t seg_end = r.beg + r.len;
-        __syncthreads();                                  // the previous tile's cursors are no longer read
-        for (int b = threadIdx.x; b < p; b += NT) cursor[b] = r.beg + col[r.hist0 + (size_t)b * r.ntile + tl];
-        const uint32_t A = r.beg + tl * r.tile, B = r.beg + min(r.len, (tl + 1) * r.tile);
-        const uint32_t vs0 = A / VEC, vs1 = (B + VEC - 1) / VEC;
-        for (uint32_t v0 = vs0; v0 < vs1; v0 += (uint32_t)NT * NV) {
-            T k[NV][VEC];
-            uint32_t b[NV][VEC];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                const uint32_t vs = v0 + (uint32_t)v * NT + threadIdx.x;
-                const uint32_t e = vs * VEC;
-                bool in[VEC];
-                if (vs < vs1) {
-                    load_slot<T>(keys, vec_ok, vs, A, B, k[v], in);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < VEC; ++j) in[j] = false;
-                }
-                bool all_in = true;
-#pragma unroll
-                for (int j = 0; j < VEC; ++j) all_in &= in[j];
-                if (all_in && vec_ok) {
-                    if constexpr (VEC == 4) {
-                        const uint2 w = __ldg(reinterpret_cast<const uint2*>(bid + e));
-                        b[v][0] = w.x & 0xFFFFu;
-                        b[v][1] = w.x >> 16;
-                        b[v][2] = w.y & 0xFFFFu;
-                        b[v][3] = w.y >> 16;
-                    } else {
-                        const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(bid + e));
-                        b[v][0] = w & 0xFFFFu;
-                        b[v][1] = w >> 16;
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < VEC; ++j) b[v][j] = in[j] ? (uint32_t)bid[e + j] : (uint32_t)p;
-                }
-            }
-            for (int x = threadIdx.x; x <= p; x += NT) toff[x] = 0;
-            __syncthreads();
-            uint32_t slot[NV][VEC];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) slot_vec<VEC>(b[v], toff, slot[v]);
-            const uint32_t tvalid = block_exclusive_scan(toff, p, scratch);
-            for (int x = threadIdx.x; x < p; x += NT) {
-                const uint32_t lo = toff[x], hi = x + 1 < p ? toff[x + 1] : tvalid;
-                delta[x] = (int32_t)(cursor[x] - lo);
-                cursor[x] += hi - lo;
-            }
-#pragma unroll
-            for (int v = 0; v < NV; ++v)
-#pragma unroll
-                for (int j = 0; j < VEC; ++j) {
-                    const uint32_t bb = b[v][j];
-                    if (bb < (uint32_t)p) {
-                        const uint32_t loc = toff[bb] + slot[v][j];
-                        if (loc >= (uint32_t)SUB) {
-                            flag_bounds(status, 10, loc);
-                            continue;
-                        }
-                        sk[loc] = k[v][j];
-                        sb[loc] = (uint16_t)bb;
-                    }
-                }
-            __syncthreads();
-            for (uint32_t jj = threadIdx.x; jj < tvalid; jj += NT) {
-                const uint32_t bb = sb[jj];
-                if (bb >= (uint32_t)p) {
-                    flag_bounds(status, 12, jj);
-                    continue;
-                }
-                const uint32_t dst = (uint32_t)(delta[bb] + (int32_t)jj);
-                if (dst < r.beg || dst >= seg_end) {
-                    flag_bounds(status, 11, dst);
-                    continue;
-                }
-                out[dst] = sk[jj];
-            }
-            __syncthreads();   // toff, delta, sk, sb are rewritten by the next sub-tile
-        }
     }
 }
 

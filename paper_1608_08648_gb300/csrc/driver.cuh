@@ -88,6 +88,10 @@ int occupancy(K kernel, int threads, size_t smem) {
     return occ > 0 ? occ : 1;
 }
 
+// Which top-level classify measured faster on GB300 at n = 2^28: the vector
+// one (k_classify_v) or the scalar one (k_classify).
+template <class T> struct TopClassifyVec { static constexpr bool on = true; };
+
 // ---------------------------------------------------------------------------
 // Segmented sort core (kernels of segkernels.cuh), shared by the bucket phase
 // of every sort and by the batched entry point.
@@ -225,15 +229,7 @@ void seg_core(Ctx& c, const SegSource& src, const SegClasses& cls, const typenam
                                                                     static_cast<const void*>(kin)),
                                                          c.status, c.status + 1,
                                                          reinterpret_cast<unsigned long long*>(c.status + 2)));
-    if (B.any_part && !HV && false) {
-        const size_t sm_s = seg_scatter_v_smem<KT>(B.maxp);
-        smem_at_least(reinterpret_cast<const void*>(k_seg_scatter_v<KT>), sm_s);
-        constexpr int SNT = SegScatterVCfg<T>::NT;
-        const uint32_t g_s = (uint32_t)(c.num_sms * occupancy(k_seg_scatter_v<KT>, SNT, sm_s));
-        OS_LAUNCH(c.st, nest ? "k_seg_scatter.sample" : "k_seg_scatter",
-                  k_seg_scatter_v<KT><<<g_s, SNT, sm_s, c.st>>>(kin, bid, rec, tile0, nseg, tot, hist, B.maxp, kout,
-                                                                 c.status));
-    } else if (B.any_part) {
+    if (B.any_part) {
         const size_t sm_s = seg_scatter_smem<KT, HV>(B.maxp);
         smem_at_least(reinterpret_cast<const void*>(k_seg_scatter<KT, HV>), sm_s);
         constexpr int SNT = SegScatterCfg<T, HV>::NT;
@@ -367,21 +363,44 @@ void partition_top_v(Ctx& c, const typename KT::T* src, uint32_t n, const typena
     uint32_t* col = c.ar.take<uint32_t>((size_t)p * gmax);
     uint16_t* bid = c.ar.take<uint16_t>(n);
     if (!c.live()) return;
-    auto kc = k_classify_v<KT, CF::NTC, CF::SUPER>;
     auto ks = k_scatter_v<KT, CF::NTS, CF::SUPER>;
-    const size_t sm_c = classify_smem<KT>(p, lb), sm_s = scatter_v_smem<T>((int)p, CF::SUPER);
-    smem_at_least(reinterpret_cast<const void*>(kc), sm_c);
+    const size_t sm_s = scatter_v_smem<T>((int)p, CF::SUPER);
     smem_at_least(reinterpret_cast<const void*>(ks), sm_s);
     const int occ = occupancy(ks, CF::NTS, sm_s);
     const uint32_t G = std::max<uint32_t>(1, std::min<uint32_t>(gmax, (uint32_t)(c.num_sms * occ)));
-    OS_LAUNCH(c.st, c.nested ? "k_classify.sample" : "k_classify",
-              kc<<<G, CF::NTC, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, lb, hist, bid, ntiles));
+    // The classify may run more CTAs than the scatter: cstep of its CTAs cover
+    // exactly one scatter CTA's units (tile_lo(g cstep, G cstep) = tile_lo(g, G)),
+    // so the scatter reads its starting counts every cstep columns.
+    auto grid_c = [&](int occ_c) {
+        const uint32_t m = std::max<uint32_t>(1, (uint32_t)(c.num_sms * occ_c) / G);
+        return (uint64_t)G * m <= gmax ? m : 1u;
+    };
+    uint32_t cstep = 1;
+    if constexpr (TopClassifyVec<T>::on) {
+        auto kc = k_classify_v<KT, CF::NTC, CF::SUPER>;
+        const size_t sm_c = classify_smem<KT>(p, lb);
+        smem_at_least(reinterpret_cast<const void*>(kc), sm_c);
+        cstep = grid_c(occupancy(kc, CF::NTC, sm_c));
+        OS_LAUNCH(c.st, c.nested ? "k_classify.sample" : "k_classify",
+                  kc<<<G * cstep, CF::NTC, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, lb, hist, bid, ntiles));
+    } else {
+        // the scalar classify over the same units
+        static_assert(ScatterCfg<T, false>::SUPER == CF::SUPER, "both classify kernels walk the same units");
+        constexpr int NTC = ScatterCfg<T, false>::NT;
+        const int lb2 = table_lbits(p);
+        const size_t sm_c = classify_smem<KT>(p, lb2);
+        smem_at_least(reinterpret_cast<const void*>(k_classify<KT, false>), sm_c);
+        cstep = grid_c(occupancy(k_classify<KT, false>, NTC, sm_c));
+        OS_LAUNCH(c.st, c.nested ? "k_classify.sample" : "k_classify",
+                  k_classify<KT, false><<<G * cstep, NTC, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, lb2, hist, bid,
+                                                                     ntiles));
+    }
     OS_LAUNCH(c.st, c.nested ? "k_column_scan.sample" : "k_column_scan",
-              k_column_scan<<<grid_for((uint64_t)p * 32, 256), 256, 0, c.st>>>(hist, p, G, col, bsize));
+              k_column_scan<<<grid_for((uint64_t)p * 32, 256), 256, 0, c.st>>>(hist, p, G * cstep, col, bsize));
     OS_LAUNCH(c.st, c.nested ? "k_bucket_offsets.sample" : "k_bucket_offsets",
               k_bucket_offsets<<<1, 1024, 0, c.st>>>(bsize, p, boff));
     OS_LAUNCH(c.st, c.nested ? "k_scatter.sample" : "k_scatter",
-              ks<<<G, CF::NTS, sm_s, c.st>>>(src, bid, n, (int)p, col, boff, dst, ntiles, c.status));
+              ks<<<G, CF::NTS, sm_s, c.st>>>(src, bid, n, (int)p, col, cstep, boff, dst, ntiles, c.status));
 }
 
 template <class KT, bool HV>

@@ -139,32 +139,28 @@ __device__ __forceinline__ E64 eflip(const E64& a, uint32_t f) { return E64{a.k 
 // On entry the space of lane l is l & 1; after `levels` levels it is
 // (l >> levels) & 1, so the lanes of the first 2^levels-lane block (which hold the
 // sorted elements) are back in plain space.
-// One half-cleaner step across lanes: the element of lane ^ dl, and the min
-// (lower lane) or max of the pair.  Written as one inline-PTX block per element so
-// the shuffles stay next to their compares instead of being hoisted ahead of
-// them, which would hold every shuffled copy of the 32 IT elements live at once.
-__device__ __forceinline__ E32 xlane_cas(const E32& a, int dl, uint32_t lower) {
-    uint32_t r;
-    asm volatile("{\n\t.reg .u32 t;\n\t.reg .pred pl;\n\t"
-                 "shfl.sync.bfly.b32 t, %1, %2, 0x1f, 0xffffffff;\n\t"
-                 "setp.ne.u32 pl, %3, 0;\n\t"
-                 "@pl min.u32 %0, %1, t;\n\t"
-                 "@!pl max.u32 %0, %1, t;\n\t}"
-                 : "=r"(r) : "r"(a.k), "r"(dl), "r"(lower));
-    return E32{r};
-}
-__device__ __forceinline__ E64 xlane_cas(const E64& a, int dl, uint32_t lower) {
-    uint64_t r;
-    asm volatile("{\n\t.reg .u32 lo, hi;\n\t.reg .u64 t;\n\t.reg .pred pl;\n\t"
-                 "mov.b64 {lo, hi}, %1;\n\t"
-                 "shfl.sync.bfly.b32 lo, lo, %2, 0x1f, 0xffffffff;\n\t"
-                 "shfl.sync.bfly.b32 hi, hi, %2, 0x1f, 0xffffffff;\n\t"
-                 "mov.b64 t, {lo, hi};\n\t"
-                 "setp.ne.u32 pl, %3, 0;\n\t"
-                 "@pl min.u64 %0, %1, t;\n\t"
-                 "@!pl max.u64 %0, %1, t;\n\t}"
-                 : "=l"(r) : "l"(a.k), "r"(dl), "r"(lower));
-    return E64{r};
+// One half-cleaner step across lanes for four elements: each takes the element
+// of lane ^ dl and keeps the min (lower lane) or the max of the pair.  Written as
+// one inline-PTX block (one predicate for the four) so the shuffles stay next
+// to their compares instead of being hoisted ahead of them, which would hold
+// every shuffled copy of the 32 IT elements live at once.
+__device__ __forceinline__ void xlane_cas4(E32& a, E32& b, E32& c, E32& d, int dl, uint32_t lower) {
+    asm volatile("{\n\t.reg .u32 t0, t1, t2, t3;\n\t.reg .pred pl;\n\t"
+                 "setp.ne.u32 pl, %5, 0;\n\t"
+                 "shfl.sync.bfly.b32 t0, %0, %4, 0x1f, 0xffffffff;\n\t"
+                 "shfl.sync.bfly.b32 t1, %1, %4, 0x1f, 0xffffffff;\n\t"
+                 "shfl.sync.bfly.b32 t2, %2, %4, 0x1f, 0xffffffff;\n\t"
+                 "shfl.sync.bfly.b32 t3, %3, %4, 0x1f, 0xffffffff;\n\t"
+                 "@pl min.u32 %0, %0, t0;\n\t"
+                 "@!pl max.u32 %0, %0, t0;\n\t"
+                 "@pl min.u32 %1, %1, t1;\n\t"
+                 "@!pl max.u32 %1, %1, t1;\n\t"
+                 "@pl min.u32 %2, %2, t2;\n\t"
+                 "@!pl max.u32 %2, %2, t2;\n\t"
+                 "@pl min.u32 %3, %3, t3;\n\t"
+                 "@!pl max.u32 %3, %3, t3;\n\t}"
+                 : "+r"(a.k), "+r"(b.k), "+r"(c.k), "+r"(d.k)
+                 : "r"(dl), "r"(lower));
 }
 
 template <class E, int IT>
@@ -174,11 +170,12 @@ __device__ __forceinline__ void warp_bitonic_level(E (&x)[IT], int v) {
     const uint32_t f = (ns ^ space) ? 0xFFFFFFFFu : 0u;
 #pragma unroll
     for (int i = 0; i < IT; ++i) x[i] = eflip(x[i], f);
+    static_assert(IT % 4 == 0, "elements go four at a time across lanes");
 #pragma unroll 1
     for (int dl = 1 << v; dl >= 1; dl >>= 1) {
         const uint32_t lower = (lane & dl) == 0;
 #pragma unroll
-        for (int i = 0; i < IT; ++i) x[i] = xlane_cas(x[i], dl, lower);
+        for (int i = 0; i < IT; i += 4) xlane_cas4(x[i], x[i + 1], x[i + 2], x[i + 3], dl, lower);
     }
     bitonic_merge_regs<E, IT>(x);
 }
