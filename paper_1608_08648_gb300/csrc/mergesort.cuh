@@ -122,28 +122,22 @@ __device__ __forceinline__ void bitonic_merge_regs(E (&x)[IT]) {
             if ((i & jj) == 0) cas_up(x[i], x[i + jj]);
 }
 
-// Order-reversing flip of a single-word element (its bits complemented) when f.
-__device__ __forceinline__ E32 eflip(const E32& a, uint32_t f) { return E32{a.k ^ f}; }
-__device__ __forceinline__ E64 eflip(const E64& a, uint32_t f) { return E64{a.k ^ (((uint64_t)f << 32) | f)}; }
-
-// Bitonic sort of a warp's 32 * IT elements held blocked (lane l has elements
-// l IT .. l IT + IT - 1 in x), from runs of IT that every lane has already sorted
-// ascending in its own "space": lanes whose space bit is set hold complemented
-// elements, so an ascending run there is a descending run of the elements.
-// Level v (v = 0 .. levels - 1) merges pairs of 2^v-lane blocks into 2^(v+1)-lane
-// blocks, the block of lanes [j 2^(v+1), (j+1) 2^(v+1)) ascending for even j and
-// descending for odd j (the alternation that makes every next pair bitonic): the
-// lanes switch to that block's space (complementing when it changes), then the
-// half-cleaners of the bitonic merge run ascending -- across lanes by shuffles
-// for distances of IT elements and more, inside the lane for the last log2(IT).
-// On entry the space of lane l is l & 1; after `levels` levels it is
-// (l >> levels) & 1, so the lanes of the first 2^levels-lane block (which hold the
-// sorted elements) are back in plain space.
-// One half-cleaner step across lanes for four elements: each takes the element
-// of lane ^ dl and keeps the min (lower lane) or the max of the pair.  Written as
-// one inline-PTX block (one predicate for the four) so the shuffles stay next
-// to their compares instead of being hoisted ahead of them, which would hold
-// every shuffled copy of the 32 IT elements live at once.
+// Bitonic merging of a warp's 32 * IT elements held blocked (lane l has elements
+// l IT .. l IT + IT - 1 in x), from runs of IT that every lane has sorted
+// ascending.  Level v (v = 0 .. levels - 1) merges pairs of ascending 2^v-lane
+// runs into ascending 2^(v+1)-lane runs with Batcher's bitonic merge, the second
+// run taken in reverse: the first stage compares every element with its mirror
+// image in the block (lane l ^ (2^(v+1) - 1), register IT - 1 - i), the lower
+// half keeping the minima -- which leaves two bitonic halves, all of the lower
+// one below all of the upper one -- and the half-cleaners that follow run
+// ascending: across lanes by shuffles for distances of IT elements and more,
+// inside the lane for the last log2(IT).
+//
+// Each inline-PTX block handles four elements with one predicate, and takes all
+// its shuffled values before it changes any of them (the mirror stage sends the
+// registers it later updates), so the shuffles stay next to their compares
+// instead of being hoisted ahead of them, which would hold every shuffled copy
+// of the 32 IT elements live at once.
 __device__ __forceinline__ void xlane_cas4(E32& a, E32& b, E32& c, E32& d, int dl, uint32_t lower) {
     asm volatile("{\n\t.reg .u32 t0, t1, t2, t3;\n\t.reg .pred pl;\n\t"
                  "setp.ne.u32 pl, %5, 0;\n\t"
@@ -163,19 +157,41 @@ __device__ __forceinline__ void xlane_cas4(E32& a, E32& b, E32& c, E32& d, int d
                  : "r"(dl), "r"(lower));
 }
 
+// The mirror stage for two pairs of registers (a, b) = (x[k], x[IT-1-k]) and
+// (c, d) = (x[k+1], x[IT-2-k]): a meets the partner's b, b the partner's a, and
+// so on, partner = lane ^ m.
+__device__ __forceinline__ void xlane_mirror4(E32& a, E32& b, E32& c, E32& d, int m, uint32_t lower) {
+    asm volatile("{\n\t.reg .u32 t0, t1, t2, t3;\n\t.reg .pred pl;\n\t"
+                 "setp.ne.u32 pl, %5, 0;\n\t"
+                 "shfl.sync.bfly.b32 t0, %1, %4, 0x1f, 0xffffffff;\n\t"
+                 "shfl.sync.bfly.b32 t1, %0, %4, 0x1f, 0xffffffff;\n\t"
+                 "shfl.sync.bfly.b32 t2, %3, %4, 0x1f, 0xffffffff;\n\t"
+                 "shfl.sync.bfly.b32 t3, %2, %4, 0x1f, 0xffffffff;\n\t"
+                 "@pl min.u32 %0, %0, t0;\n\t"
+                 "@!pl max.u32 %0, %0, t0;\n\t"
+                 "@pl min.u32 %1, %1, t1;\n\t"
+                 "@!pl max.u32 %1, %1, t1;\n\t"
+                 "@pl min.u32 %2, %2, t2;\n\t"
+                 "@!pl max.u32 %2, %2, t2;\n\t"
+                 "@pl min.u32 %3, %3, t3;\n\t"
+                 "@!pl max.u32 %3, %3, t3;\n\t}"
+                 : "+r"(a.k), "+r"(b.k), "+r"(c.k), "+r"(d.k)
+                 : "r"(m), "r"(lower));
+}
+
 template <class E, int IT>
 __device__ __forceinline__ void warp_bitonic_level(E (&x)[IT], int v) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t space = (lane >> v) & 1, ns = (lane >> (v + 1)) & 1;
-    const uint32_t f = (ns ^ space) ? 0xFFFFFFFFu : 0u;
-#pragma unroll
-    for (int i = 0; i < IT; ++i) x[i] = eflip(x[i], f);
     static_assert(IT % 4 == 0, "elements go four at a time across lanes");
-#pragma unroll 1
-    for (int dl = 1 << v; dl >= 1; dl >>= 1) {
-        const uint32_t lower = (lane & dl) == 0;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lower = (lane & (1 << v)) == 0;             // lower half of the 2^(v+1)-lane block
+    const int m = (2 << v) - 1;
 #pragma unroll
-        for (int i = 0; i < IT; i += 4) xlane_cas4(x[i], x[i + 1], x[i + 2], x[i + 3], dl, lower);
+    for (int k = 0; k < IT / 2; k += 2) xlane_mirror4(x[k], x[IT - 1 - k], x[k + 1], x[IT - 2 - k], m, lower);
+#pragma unroll 1
+    for (int dl = 1 << v >> 1; dl >= 1; dl >>= 1) {
+        const uint32_t lo = (lane & dl) == 0;
+#pragma unroll
+        for (int i = 0; i < IT; i += 4) xlane_cas4(x[i], x[i + 1], x[i + 2], x[i + 3], dl, lo);
     }
     bitonic_merge_regs<E, IT>(x);
 }
@@ -201,11 +217,7 @@ __device__ __forceinline__ void merge_sort_block(E (&x)[IT], E* sk, int len) {
     const bool active = base < len;
     int run0 = IT;
     if constexpr (sizeof(E) == 4) {
-        // every lane sorts (padding included: the shuffles need the whole warp),
-        // odd lanes in complemented space
-        const uint32_t f = (threadIdx.x & 1) ? 0xFFFFFFFFu : 0u;
-#pragma unroll
-        for (int i = 0; i < IT; ++i) x[i] = eflip(x[i], f);
+        // every lane sorts (padding included: the shuffles need the whole warp)
         oddeven_sort_regs<E, IT>(x);
         const int wlen = min(len, 32 * IT);     // elements the warps must order among themselves
         int levels = 0;
