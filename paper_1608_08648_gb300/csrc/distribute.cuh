@@ -379,32 +379,11 @@ k_scatter_v(const typename KT::T* __restrict__ keys, const uint16_t* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// The bucket phase's split (k_seg_classify / k_seg_scatter of segkernels.cuh)
-// over 16-byte vectors.  A tile [A, B) of absolute positions starts anywhere, so
-// both kernels walk the vector slots [floor(A / VEC), ceil(B / VEC)) of the key
-// array: a slot wholly inside the tile is one vector load, the (at most two)
-// partial slots at the ends are loaded key by key, and keys outside the tile
-// take the spare bucket id p.
+// The bucket phase's classify (k_seg_classify of segkernels.cuh) over 16-byte
+// vectors.  A tile [A, B) of absolute positions starts anywhere: the whole
+// vector slots inside it are loaded as vectors, the at most VEC - 1 keys at
+// either end one by one.
 // ---------------------------------------------------------------------------
-
-// The keys of vector slot vs that lie in [A, B): k[j] and whether it is in.
-template <class T>
-__device__ __forceinline__ void load_slot(const T* __restrict__ keys, bool vec_ok, uint32_t vs, uint32_t A, uint32_t B,
-                                          T (&k)[VecOf<T>::N], bool (&in)[VecOf<T>::N]) {
-    constexpr int VEC = VecOf<T>::N;
-    const uint32_t e = vs * VEC;
-    if (vec_ok && e >= A && e + VEC <= B) {
-        unpack16<T>(__ldg(reinterpret_cast<const uint4*>(keys + e)), k);
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) in[j] = true;
-    } else {
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) {
-            in[j] = e + j >= A && e + j < B;
-            k[j] = in[j] ? keys[e + j] : T(0);
-        }
-    }
-}
 
 template <class KT>
 size_t seg_classify_v_smem(int maxp) {
@@ -459,42 +438,49 @@ k_seg_classify_v(const typename KT::T* __restrict__ keys, const SegRec* __restri
         for (int b = threadIdx.x; b <= p; b += SEG_NT) cnt[b] = 0;
         __syncthreads();
         const uint32_t A = r.beg + tl * r.tile, B = r.beg + min(r.len, (tl + 1) * r.tile);
-        const uint32_t vs0 = A / VEC, vs1 = (B + VEC - 1) / VEC;
-        for (uint32_t v0 = vs0; v0 < vs1; v0 += (uint32_t)SEG_NT * R) {
-            T k[R][VEC];
-            bool in[R][VEC];
+        // whole vector slots [fa, fb) without range tests; the at most 2 (VEC - 1)
+        // keys of [A, B) outside them (and every key when the keys are not
+        // 16-byte aligned) key by key
+        const uint32_t fa = vec_ok ? (A + VEC - 1) / VEC : B / VEC + 1;
+        const uint32_t fb = vec_ok ? max(B / VEC, fa) : fa;
+        for (uint32_t v0 = fa; v0 < fb; v0 += (uint32_t)SEG_NT * R) {
+            uint4 raw[R];
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 const uint32_t vs = v0 + (uint32_t)q * SEG_NT + threadIdx.x;
-                if (vs < vs1) {
-                    load_slot<T>(keys, vec_ok, vs, A, B, k[q], in[q]);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < VEC; ++j) in[q][j] = false;
-                }
+                if (vs < fb) raw[q] = __ldg(reinterpret_cast<const uint4*>(keys + (size_t)vs * VEC));
             }
 #pragma unroll
             for (int q = 0; q < R; ++q) {
-                const uint32_t e = (v0 + (uint32_t)q * SEG_NT + threadIdx.x) * VEC;
+                const uint32_t vs = v0 + (uint32_t)q * SEG_NT + threadIdx.x;
+                const uint32_t e = vs * VEC;
                 uint32_t b[VEC];
-                bool all_in = true;
+                if (vs < fb) {
+                    T k[VEC];
+                    unpack16<T>(raw[q], k);
 #pragma unroll
-                for (int j = 0; j < VEC; ++j) {
-                    b[j] = in[q][j] ? (uint32_t)split_find_clamped<O>(tb, KT::ord(k[q][j]), e + j - r.beg, last_bin)
-                                    : (uint32_t)p;
-                    all_in &= in[q][j];
-                }
-                if (all_in) {
+                    for (int j = 0; j < VEC; ++j)
+                        b[j] = (uint32_t)split_find_clamped<O>(tb, KT::ord(k[j]), e + j - r.beg, last_bin);
                     if constexpr (VEC == 4)
                         *reinterpret_cast<uint2*>(bid + e) = make_uint2(b[0] | (b[1] << 16), b[2] | (b[3] << 16));
                     else
                         *reinterpret_cast<uint32_t*>(bid + e) = b[0] | (b[1] << 16);
                 } else {
 #pragma unroll
-                    for (int j = 0; j < VEC; ++j)
-                        if (in[q][j]) bid[e + j] = (uint16_t)b[j];
+                    for (int j = 0; j < VEC; ++j) b[j] = (uint32_t)p;     // the spare counter
                 }
                 count_vec<VEC>(b, cnt);
+            }
+        }
+        {
+            const uint32_t lo_end = min(B, fa * VEC);                 // keys [A, lo_end) before the slots
+            const uint32_t hi_beg = max(lo_end, min(B, fb * VEC));    // keys [hi_beg, B) after them
+            const uint32_t nlo = lo_end - A, nedge = nlo + (B - hi_beg);
+            for (uint32_t i = threadIdx.x; i < nedge; i += SEG_NT) {
+                const uint32_t e = i < nlo ? A + i : hi_beg + (i - nlo);
+                const uint32_t bk = (uint32_t)split_find_clamped<O>(tb, KT::ord(keys[e]), e - r.beg, last_bin);
+                bid[e] = (uint16_t)bk;
+                atomicAdd(&cnt[bk], 1u);
             }
         }
         __syncthreads();
