@@ -192,6 +192,23 @@ def measured_traffic(kernel: str, dtype: str, n: int):
     return int(t["dram_bytes_per_key"][kernel] * n)
 
 
+def measured_pipe(kernel: str, dtype: str):
+    """The secondary bound of a compute-bound kernel from the committed ncu capture:
+    its ALU-pipe and issue activity (% of peak); None when the kernels changed since
+    the capture or no capture exists."""
+    path = os.path.join(ROOT, "profiles", f"kernel_traffic_{dtype}.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except OSError:
+        return None
+    pipes = t.get("pipes", {})
+    if t.get("source_sha") != cuda_source_sha() or kernel not in pipes:
+        return None
+    return dict(pipes[kernel], source="profiles/" + os.path.basename(path) + " (ncu --set full, one launch at "
+                f"{t.get('n_captured')} keys)")
+
+
 def algorithmic_bytes(name: str, n: int, kb: int, vb: int, repart_keys: int, split_keys: int = 0) -> int:
     """Bytes a kernel must move for one step (one full sort of n keys), the minimum
     ledger of one distribution level (no stored bucket ids): classify reads every key;
@@ -953,6 +970,7 @@ def time_sort(a, dtype, p, rank, world, local, steps, warmup, with_e2e=True):
                 "alg_bytes_per_step": algorithmic_bytes(dom["name"], n, kb, vb, st["repart_keys"], split_keys),
                 "timing": "CUDA events around every launch of the kernel on its stream, in a second pass of the "
                           "same steps with the library's event profiler on",
+                "secondary": measured_pipe(dom["name"], dtype),
                 "pipeline": pipeline_ledger(n, kb, vb, split_keys, st["repart_keys"], ms, peak, dtype, p)}
     return {"n": n, "dtype": dtype, "p": p, "value": value, "ms": ms, "roofline": roof, "e2e": e2e,
             "launches": launches, "clocks": clk, "prof": prof, "prof_ms": prof_ms, "stats": st,

@@ -88,10 +88,6 @@ int occupancy(K kernel, int threads, size_t smem) {
     return occ > 0 ? occ : 1;
 }
 
-// Which top-level classify measured faster on GB300 at n = 2^28: the vector
-// one (k_classify_v) or the scalar one (k_classify).
-template <class T> struct TopClassifyVec { static constexpr bool on = true; };
-
 // ---------------------------------------------------------------------------
 // Segmented sort core (kernels of segkernels.cuh), shared by the bucket phase
 // of every sort and by the batched entry point.
@@ -335,11 +331,16 @@ size_t scatter_smem(int p) {
 // Bucket b occupies [boff[b], boff[b+1]); bsize[b] = its size.
 // Keys without a payload take the vector passes of distribute.cuh: units of
 // SUPER keys, classify with NTC threads, scatter with NTS threads holding
-// SUPER / NTS keys each (16 for 4-byte keys, 8 for 8-byte keys).
-template <class T> struct TopVCfg {
-    static constexpr int SUPER = 8192;
+// SUPER / NTS keys each.  Measured best on GB300 (units of 4096-16384 keys):
+// 4-byte keys 16384-key units with 1024 threads (the scatter's two unit buffers
+// then fill most of an SM's shared memory, one CTA per SM), as long as p <= 2048
+// leaves room for its counters, else 8192-key units with 512 threads; 8-byte keys
+// 8192-key units with 1024 threads.  The choice depends on p alone, so the
+// workspace plan and the launches agree.
+template <int SUPER_, int NTS_> struct TopVCfg {
+    static constexpr int SUPER = SUPER_;
     static constexpr int NTC = 512;
-    static constexpr int NTS = sizeof(T) == 4 ? 512 : 1024;
+    static constexpr int NTS = NTS_;
 };
 
 // Bins of the vector classify's splitter table: the power of two >= 4p (at most
@@ -350,11 +351,10 @@ inline int table_lbits_v(uint32_t p) {
     return b;
 }
 
-template <class KT>
-void partition_top_v(Ctx& c, const typename KT::T* src, uint32_t n, const typename KT::O* spl_o,
-                     const uint32_t* spl_t, uint32_t p, typename KT::T* dst, uint32_t* boff, uint32_t* bsize) {
+template <class KT, class CF>
+void partition_top_v_cfg(Ctx& c, const typename KT::T* src, uint32_t n, const typename KT::O* spl_o,
+                         const uint32_t* spl_t, uint32_t p, typename KT::T* dst, uint32_t* boff, uint32_t* bsize) {
     using T = typename KT::T;
-    using CF = TopVCfg<T>;
     constexpr uint32_t SUPER = CF::SUPER;
     const int lb = table_lbits_v(p);
     const uint32_t ntiles = (n + SUPER - 1) / SUPER;
@@ -375,32 +375,29 @@ void partition_top_v(Ctx& c, const typename KT::T* src, uint32_t n, const typena
         const uint32_t m = std::max<uint32_t>(1, (uint32_t)(c.num_sms * occ_c) / G);
         return (uint64_t)G * m <= gmax ? m : 1u;
     };
-    uint32_t cstep = 1;
-    if constexpr (TopClassifyVec<T>::on) {
-        auto kc = k_classify_v<KT, CF::NTC, CF::SUPER>;
-        const size_t sm_c = classify_smem<KT>(p, lb);
-        smem_at_least(reinterpret_cast<const void*>(kc), sm_c);
-        cstep = grid_c(occupancy(kc, CF::NTC, sm_c));
-        OS_LAUNCH(c.st, c.nested ? "k_classify.sample" : "k_classify",
-                  kc<<<G * cstep, CF::NTC, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, lb, hist, bid, ntiles));
-    } else {
-        // the scalar classify over the same units
-        static_assert(ScatterCfg<T, false>::SUPER == CF::SUPER, "both classify kernels walk the same units");
-        constexpr int NTC = ScatterCfg<T, false>::NT;
-        const int lb2 = table_lbits(p);
-        const size_t sm_c = classify_smem<KT>(p, lb2);
-        smem_at_least(reinterpret_cast<const void*>(k_classify<KT, false>), sm_c);
-        cstep = grid_c(occupancy(k_classify<KT, false>, NTC, sm_c));
-        OS_LAUNCH(c.st, c.nested ? "k_classify.sample" : "k_classify",
-                  k_classify<KT, false><<<G * cstep, NTC, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, lb2, hist, bid,
-                                                                     ntiles));
-    }
+    auto kc = k_classify_v<KT, CF::NTC, CF::SUPER>;
+    const size_t sm_c = classify_smem<KT>(p, lb);
+    smem_at_least(reinterpret_cast<const void*>(kc), sm_c);
+    const uint32_t cstep = grid_c(occupancy(kc, CF::NTC, sm_c));
+    OS_LAUNCH(c.st, c.nested ? "k_classify.sample" : "k_classify",
+              kc<<<G * cstep, CF::NTC, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, lb, hist, bid, ntiles));
     OS_LAUNCH(c.st, c.nested ? "k_column_scan.sample" : "k_column_scan",
               k_column_scan<<<grid_for((uint64_t)p * 32, 256), 256, 0, c.st>>>(hist, p, G * cstep, col, bsize));
     OS_LAUNCH(c.st, c.nested ? "k_bucket_offsets.sample" : "k_bucket_offsets",
               k_bucket_offsets<<<1, 1024, 0, c.st>>>(bsize, p, boff));
     OS_LAUNCH(c.st, c.nested ? "k_scatter.sample" : "k_scatter",
               ks<<<G, CF::NTS, sm_s, c.st>>>(src, bid, n, (int)p, col, cstep, boff, dst, ntiles, c.status));
+}
+
+template <class KT>
+void partition_top_v(Ctx& c, const typename KT::T* src, uint32_t n, const typename KT::O* spl_o,
+                     const uint32_t* spl_t, uint32_t p, typename KT::T* dst, uint32_t* boff, uint32_t* bsize) {
+    if constexpr (sizeof(typename KT::T) == 4) {
+        if (p <= 2048) partition_top_v_cfg<KT, TopVCfg<16384, 1024>>(c, src, n, spl_o, spl_t, p, dst, boff, bsize);
+        else partition_top_v_cfg<KT, TopVCfg<8192, 512>>(c, src, n, spl_o, spl_t, p, dst, boff, bsize);
+    } else {
+        partition_top_v_cfg<KT, TopVCfg<8192, 1024>>(c, src, n, spl_o, spl_t, p, dst, boff, bsize);
+    }
 }
 
 template <class KT, bool HV>

@@ -36,3 +36,16 @@ def test_traffic_used_only_for_its_sources(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "cuda_source_sha", lambda: "0" * 16)
     assert bench.measured_traffic("k_leaf", "i32", 1000) is None
     assert bench.measured_traffic("k_leaf", "f64", 1000) is None      # no capture for float64
+
+
+def test_secondary_bound_used_only_for_its_sources(monkeypatch):
+    path = os.path.join(bench.ROOT, "profiles", "kernel_traffic_i32.json")
+    with open(path) as f:
+        t = json.load(f)
+    monkeypatch.setattr(bench, "cuda_source_sha", lambda: t["source_sha"])
+    sec = bench.measured_pipe("k_leaf", "i32")
+    if "pipes" in t:
+        assert sec is not None and 0 < sec["alu_pipe_pct"] <= 100 and "ncu" in sec["source"]
+    monkeypatch.setattr(bench, "cuda_source_sha", lambda: "0" * 16)
+    assert bench.measured_pipe("k_leaf", "i32") is None
+    assert bench.measured_pipe("k_leaf", "f64") is None

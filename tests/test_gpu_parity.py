@@ -160,3 +160,25 @@ def test_status_word_clean_after_sorts():
     rc_, bits = oss.os_check(ws.data_ptr(), torch.cuda.current_stream().cuda_stream)
     assert rc_ == oss.OS_OK and bits == 0
     assert torch.equal(out, torch.sort(keys).values)
+
+
+@pytest.mark.parametrize("kt", ["i32", "f64"])
+@pytest.mark.parametrize("shift", [1, 3])
+def test_keys_not_16_byte_aligned(kt, shift):
+    """Input and output arrays that start off a 16-byte boundary (views into larger
+    tensors): the vector passes fall back to loads of one key; the result is the
+    oracle's for the same keys."""
+    n = (1 << 20) + 17
+    keys = gen("uniform", n, kt, seed=11 + shift)
+    big = torch.from_numpy(np.concatenate([np.zeros(shift, keys.dtype), keys, np.zeros(5, keys.dtype)])).cuda()
+    d = big[shift:shift + n]
+    outbig = torch.empty_like(big)
+    out = outbig[shift:shift + n]
+    assert d.data_ptr() % 16 != 0 and out.data_ptr() % 16 != 0
+    for split, p, s in (("ran", 64, 8), ("det", 32, 4)):
+        ref = oracle.sort(keys, kt, split, p, s, seed=5)
+        ko, _, st = oss.sort(d, None, split=split, p=p, s=s, seed=5, out=out, key_type=kt, stats=True)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_np(ko, kt).view(np.uint8), ref["keys"].view(np.uint8)), f"{split}: keys differ"
+        assert np.array_equal(st["bucket_sizes"], ref["bucket_sizes"])
+        assert np.array_equal(st["spl_tags"], ref["spl_tags"])
