@@ -198,7 +198,7 @@ namespace {
 // (a.res.sunk tells whether it did).
 int sort_device(int key_type, const void* d_keys_in, void* d_keys_out, const uint32_t* d_vals_in,
                 uint32_t* d_vals_out, uint64_t n, const os_params* prm, void* d_ws, size_t ws_bytes, void* stream,
-                os_stats* stats, const HostSink* sink, RunArgs& a) {
+                os_stats* stats, const HostSink* sink, RunArgs& a, void* kin_copy = nullptr) {
     int rc = check_params(key_type, n, prm);
     if (rc) return rc;
     if (n > 0 && (!d_keys_in || !d_keys_out)) return OS_ERR_ARG;
@@ -219,6 +219,7 @@ int sort_device(int key_type, const void* d_keys_in, void* d_keys_out, const uin
     a.st = static_cast<cudaStream_t>(stream);
     a.num_sms = num_sms_of_current_device();
     a.sink = sink;
+    a.kin_copy = kin_copy;
     rc = dispatch(key_type, a);
     if (rc) return rc;
     cudaError_t e = cudaGetLastError();
@@ -361,7 +362,21 @@ int os_sort_host(int key_type, const void* h_keys_in, void* h_keys_out, const ui
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t kbytes = n * key_bytes(key_type);
     cudaError_t e = cudaSuccess;
-    if (n > 0) {
+    // Keys alone, SqRan, large enough to sample: when the device can address the
+    // host buffer (page-locked memory: the host link of a Grace-Blackwell node is
+    // coherent), the sort reads the keys from it directly -- the sample by a
+    // gather, the top-level classify by a pass that also leaves the device copy
+    // the scatter uses -- instead of waiting for a separate copy-in first.
+    const void* hdev = nullptr;
+    if (!hv && key_type != OS_S32 && prm->split == OS_RAN && prm->p > 1 && n >= HOST_CHUNK_MIN_N &&
+        n >= 2ull * prm->p * prm->s) {
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, h_keys_in) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer != nullptr)
+            hdev = pa.devicePointer;
+        cudaGetLastError();
+    }
+    if (n > 0 && !hdev) {
         e = cudaMemcpyAsync(dk, h_keys_in, kbytes, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess && hv) e = cudaMemcpyAsync(dv, h_vals_in, n * 4, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e);
@@ -374,8 +389,8 @@ int os_sort_host(int key_type, const void* h_keys_in, void* h_keys_out, const ui
         sink.chunks = sink.copy ? HOST_CHUNKS : 1u;
     }
     RunArgs a{};
-    rc = sort_device(key_type, dk, dk, dv, dv, n, prm, d_ws, inner, stream, nullptr, sink.chunks > 1 ? &sink : nullptr,
-                     a);
+    rc = sort_device(key_type, hdev ? hdev : dk, dk, dv, dv, n, prm, d_ws, inner, stream, nullptr,
+                     sink.chunks > 1 ? &sink : nullptr, a, hdev ? dk : nullptr);
     if (rc) return rc;
     if (n > 0 && !a.res.sunk) {
         e = cudaMemcpyAsync(h_keys_out, dk, kbytes, cudaMemcpyDeviceToHost, st);

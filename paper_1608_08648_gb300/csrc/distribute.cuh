@@ -111,12 +111,13 @@ __device__ __forceinline__ void slot_vec(const uint32_t (&b)[VEC], uint32_t* cnt
 
 // Classify, keys only or with a payload (the payload does not take part).
 // Threads NT, units of SUPER keys (the scatter's).  hist is bucket-major:
-// hist[b * G + g].
+// hist[b * G + g].  copy: NULL, or a device array that receives every key as it
+// is read (the keys then come from host memory over the host link, read once).
 template <class KT, int NT, int SUPER>
 __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : (NT >= 512 ? 2 : 4))
 k_classify_v(const typename KT::T* __restrict__ keys, uint32_t n, const typename KT::O* __restrict__ spl_o,
              const uint32_t* __restrict__ spl_t, int p, int lbits, uint32_t* __restrict__ hist,
-             uint16_t* __restrict__ bid, uint32_t ntiles) {
+             uint16_t* __restrict__ bid, uint32_t ntiles, typename KT::T* __restrict__ copy) {
     using T = typename KT::T;
     using O = typename KT::O;
     constexpr int VEC = VecOf<T>::N;
@@ -144,10 +145,15 @@ k_classify_v(const typename KT::T* __restrict__ keys, uint32_t n, const typename
                 const uint32_t e = e0 + ((uint32_t)r * NT + threadIdx.x) * VEC;
                 if (e + VEC <= e_hi) {
                     raw[r] = __ldg(reinterpret_cast<const uint4*>(keys + e));
+                    if (copy) *reinterpret_cast<uint4*>(copy + e) = raw[r];
                 } else {
                     T tk[VEC];
 #pragma unroll
                     for (int j = 0; j < VEC; ++j) tk[j] = e + j < e_hi ? keys[e + j] : T(0);
+                    if (copy)
+#pragma unroll
+                        for (int j = 0; j < VEC; ++j)
+                            if (e + j < e_hi) copy[e + j] = tk[j];
                     if constexpr (sizeof(T) == 4)
                         raw[r] = make_uint4((uint32_t)tk[0], (uint32_t)tk[1], (uint32_t)tk[2], (uint32_t)tk[3]);
                     else
@@ -187,7 +193,9 @@ k_classify_v(const typename KT::T* __restrict__ keys, uint32_t n, const typename
                 const uint32_t e = e0 + (uint32_t)r * NT + threadIdx.x;
                 b[r] = p;
                 if (e < e_hi) {
-                    b[r] = (uint32_t)split_find_clamped<O>(tb, KT::ord(keys[e]), e, last_bin);
+                    const T k = keys[e];
+                    if (copy) copy[e] = k;
+                    b[r] = (uint32_t)split_find_clamped<O>(tb, KT::ord(k), e, last_bin);
                     bid[e] = (uint16_t)b[r];
                 }
             }

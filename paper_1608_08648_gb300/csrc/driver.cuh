@@ -351,9 +351,13 @@ inline int table_lbits_v(uint32_t p) {
     return b;
 }
 
+// copy: NULL, or a device buffer of n keys that the classify fills with the keys
+// it reads (src then lies in host memory the device reads over the host link,
+// once); the scatter reads the copy.
 template <class KT, class CF>
 void partition_top_v_cfg(Ctx& c, const typename KT::T* src, uint32_t n, const typename KT::O* spl_o,
-                         const uint32_t* spl_t, uint32_t p, typename KT::T* dst, uint32_t* boff, uint32_t* bsize) {
+                         const uint32_t* spl_t, uint32_t p, typename KT::T* dst, uint32_t* boff, uint32_t* bsize,
+                         typename KT::T* copy) {
     using T = typename KT::T;
     constexpr uint32_t SUPER = CF::SUPER;
     const int lb = table_lbits_v(p);
@@ -380,23 +384,27 @@ void partition_top_v_cfg(Ctx& c, const typename KT::T* src, uint32_t n, const ty
     smem_at_least(reinterpret_cast<const void*>(kc), sm_c);
     const uint32_t cstep = grid_c(occupancy(kc, CF::NTC, sm_c));
     OS_LAUNCH(c.st, c.nested ? "k_classify.sample" : "k_classify",
-              kc<<<G * cstep, CF::NTC, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, lb, hist, bid, ntiles));
+              kc<<<G * cstep, CF::NTC, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, lb, hist, bid, ntiles, copy));
     OS_LAUNCH(c.st, c.nested ? "k_column_scan.sample" : "k_column_scan",
               k_column_scan<<<grid_for((uint64_t)p * 32, 256), 256, 0, c.st>>>(hist, p, G * cstep, col, bsize));
     OS_LAUNCH(c.st, c.nested ? "k_bucket_offsets.sample" : "k_bucket_offsets",
               k_bucket_offsets<<<1, 1024, 0, c.st>>>(bsize, p, boff));
     OS_LAUNCH(c.st, c.nested ? "k_scatter.sample" : "k_scatter",
-              ks<<<G, CF::NTS, sm_s, c.st>>>(src, bid, n, (int)p, col, cstep, boff, dst, ntiles, c.status));
+              ks<<<G, CF::NTS, sm_s, c.st>>>(copy ? copy : src, bid, n, (int)p, col, cstep, boff, dst, ntiles,
+                                             c.status));
 }
 
 template <class KT>
 void partition_top_v(Ctx& c, const typename KT::T* src, uint32_t n, const typename KT::O* spl_o,
-                     const uint32_t* spl_t, uint32_t p, typename KT::T* dst, uint32_t* boff, uint32_t* bsize) {
+                     const uint32_t* spl_t, uint32_t p, typename KT::T* dst, uint32_t* boff, uint32_t* bsize,
+                     typename KT::T* copy = nullptr) {
     if constexpr (sizeof(typename KT::T) == 4) {
-        if (p <= 2048) partition_top_v_cfg<KT, TopVCfg<16384, 1024>>(c, src, n, spl_o, spl_t, p, dst, boff, bsize);
-        else partition_top_v_cfg<KT, TopVCfg<8192, 512>>(c, src, n, spl_o, spl_t, p, dst, boff, bsize);
+        if (p <= 2048)
+            partition_top_v_cfg<KT, TopVCfg<16384, 1024>>(c, src, n, spl_o, spl_t, p, dst, boff, bsize, copy);
+        else
+            partition_top_v_cfg<KT, TopVCfg<8192, 512>>(c, src, n, spl_o, spl_t, p, dst, boff, bsize, copy);
     } else {
-        partition_top_v_cfg<KT, TopVCfg<8192, 1024>>(c, src, n, spl_o, spl_t, p, dst, boff, bsize);
+        partition_top_v_cfg<KT, TopVCfg<8192, 1024>>(c, src, n, spl_o, spl_t, p, dst, boff, bsize, copy);
     }
 }
 
@@ -601,9 +609,15 @@ void sort_buckets(Ctx& c, const uint32_t* boff, uint32_t p, uint32_t n, typename
     res.sunk = true;
 }
 
+// kin_copy (keys alone, SqRan only): kin lies in host memory the device can
+// read; the sample is gathered from it directly and the top-level classify
+// copies the keys into kin_copy (a device buffer of n keys, may be kout) as it
+// reads them, so the keys cross the host link once and no separate copy-in
+// precedes the sort.
 template <class KT, bool HV>
 void sort_top(Ctx& c, const typename KT::T* kin, typename KT::T* kout, const uint32_t* vin, uint32_t* vout,
-              uint32_t n, const os_params& prm, TopResult& res, const HostSink* sink = nullptr) {
+              uint32_t n, const os_params& prm, TopResult& res, const HostSink* sink = nullptr,
+              typename KT::T* kin_copy = nullptr) {
     using T = typename KT::T;
     using O = typename KT::O;
     const uint32_t p = prm.p, s = prm.s;
@@ -628,7 +642,11 @@ void sort_top(Ctx& c, const typename KT::T* kin, typename KT::T* kout, const uin
     uint32_t* vw1 = HV ? c.ar.take<uint32_t>(n) : nullptr;
     if (prm.split == OS_RAN) {
         splitters_ran<KT>(c, kin, n, p, s, prm.seed, spl_o, spl_t);
-        partition_top<KT, HV>(c, kin, vin, n, spl_o, spl_t, p, w1, vw1, boff, bsize);
+        if constexpr (!HV) {
+            partition_top_v<KT>(c, kin, n, spl_o, spl_t, p, w1, boff, bsize, kin_copy);
+        } else {
+            partition_top<KT, HV>(c, kin, vin, n, spl_o, spl_t, p, w1, vw1, boff, bsize);
+        }
         sort_buckets<KT, HV>(c, boff, p, n, w1, vw1, kout, vout, w1, vw1, internal_seed, sink, res);
     } else {
         T* w2 = c.ar.take<T>(n);
@@ -661,6 +679,7 @@ struct RunArgs {
     cudaStream_t st;
     int num_sms;
     const HostSink* sink;   // host-buffer sorts: where ranges of the output go as they finish
+    void* kin_copy;         // host-buffer sorts read straight from host memory: the device copy (see sort_top)
     // outputs
     size_t used;
     uint32_t* status;
@@ -680,7 +699,8 @@ int run_sort(RunArgs& a) {
     const T* kin = static_cast<const T*>(a.kin);
     T* kout = static_cast<T*>(a.kout);
     if (a.has_vals) sort_top<KT, true>(c, kin, kout, a.vin, a.vout, (uint32_t)a.n, a.prm, a.res, a.sink);
-    else sort_top<KT, false>(c, kin, kout, nullptr, nullptr, (uint32_t)a.n, a.prm, a.res, a.sink);
+    else sort_top<KT, false>(c, kin, kout, nullptr, nullptr, (uint32_t)a.n, a.prm, a.res, a.sink,
+                             static_cast<T*>(a.kin_copy));
     a.used = c.ar.used;
     a.status = c.status;
     return c.ar.failed ? OS_ERR_WS : OS_OK;

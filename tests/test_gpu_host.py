@@ -46,3 +46,28 @@ def test_host_buffers_equal_device_sort(kt, split, n):
         assert torch.equal(h_out.view(view), d_out.cpu().view(view)), f"{kt} {split} n={n}: keys differ"
         if with_vals:
             assert torch.equal(h_vout, d_vout.cpu()), f"{kt} {split} n={n}: payload differs"
+
+
+@pytest.mark.parametrize("kt", ["i32", "f64"])
+def test_host_buffers_in_place_and_pageable(kt):
+    # page-locked input sorted in place (the sort reads it directly and writes the
+    # result back into it), and a pageable input (copied in first)
+    n = (1 << 22) + 7
+    keys = inputs.keys("uniform", n, kt, seed=21, device="cuda")
+    d_out, _, _ = oss.sort(keys, split="ran", p=512, s=16, seed=4, key_type=kt)
+    torch.cuda.synchronize()
+    view = torch.int32 if kt == "i32" else torch.int64
+    prm = oss.params("ran", 512, 16, 4)
+    rc, need = oss.os_workspace_size_host(oss.KEY_TYPES[kt], n, False, prm)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    h = keys.cpu().pin_memory()
+    assert oss.os_sort_host(oss.KEY_TYPES[kt], h.data_ptr(), h.data_ptr(), None, None, n, prm, ws.data_ptr(), need,
+                            st) == 0
+    assert torch.equal(h.view(view), d_out.cpu().view(view))
+    pg = keys.cpu()
+    assert not pg.is_pinned()
+    out = torch.empty_like(pg)
+    assert oss.os_sort_host(oss.KEY_TYPES[kt], pg.data_ptr(), out.data_ptr(), None, None, n, prm, ws.data_ptr(), need,
+                            st) == 0
+    assert torch.equal(out.view(view), d_out.cpu().view(view))
