@@ -2,6 +2,8 @@
 // on the key type, statistics and the host-buffer variant.
 #include <atomic>
 #include <cstdio>
+#include <map>
+#include <tuple>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -120,14 +122,32 @@ int dispatch(int kt, RunArgs& a) {
     }
 }
 
+// Workspace bytes of one sort: the planning pass (the driver run with a measuring
+// arena).  Its result depends on the key type, n, the payload and p, s, split and
+// flags (not on the seed, the device or the buffers), so the last results are kept
+// in a small cache under a lock: a caller sorting many arrays of a few shapes
+// plans each shape once.
 size_t plan_bytes(int kt, uint64_t n, bool has_vals, const os_params* prm) {
+    using Key = std::tuple<int, uint64_t, bool, int32_t, uint32_t, uint32_t, uint32_t>;
+    static std::mutex mu;
+    static std::map<Key, size_t> cache;
+    const Key key{kt, n, has_vals, prm->split, prm->p, prm->s, prm->flags};
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
     RunArgs a{};
     a.n = n;
     a.has_vals = has_vals;
     a.prm = *prm;
     a.ws = nullptr;
     dispatch(kt, a);
-    return a.used + 256;
+    const size_t bytes = a.used + 256;
+    std::lock_guard<std::mutex> lk(mu);
+    if (cache.size() >= 4096) cache.clear();
+    cache[key] = bytes;
+    return bytes;
 }
 
 template <class KT>
