@@ -170,9 +170,12 @@ int os_workspace_size_host(int key_type, uint64_t n, int has_vals, const os_para
  * workspace, sorts, copies the result back and synchronizes the stream.  From
  * 2^22 keys on (except 32-byte strings) the buckets are sorted in eight ranges
  * and each range is copied back, on a stream the library creates once per
- * device, while the later ranges are still being sorted.  Host buffers should
- * be pinned for full copy bandwidth; h_keys_out may equal h_keys_in.  Returns
- * OS_ERR_DEVICE if a kernel flagged an error.
+ * device, while the later ranges are still being sorted.  An OS_RAN sort of
+ * keys alone from page-locked (device-addressable) host memory skips the
+ * copy-in: it gathers its sample from the host buffer and its first classify
+ * pass reads the keys from there once, writing the device copy as it goes.
+ * Host buffers should be pinned for full copy bandwidth; h_keys_out may equal
+ * h_keys_in.  Returns OS_ERR_DEVICE if a kernel flagged an error.
  */
 int os_sort_host(int key_type, const void* h_keys_in, void* h_keys_out,
                  const uint32_t* h_vals_in, uint32_t* h_vals_out, uint64_t n,
