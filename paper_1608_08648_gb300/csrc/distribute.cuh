@@ -341,35 +341,31 @@ k_scatter_v(const typename KT::T* __restrict__ keys, const uint16_t* __restrict_
             delta[x] = (int32_t)(cursor[x] - lo);
             cursor[x] += hi - lo;
         }
+        // Range checks without a branch per key: every access is predicated on
+        // its check, and a failed check is reported once per thread afterwards.
+        uint32_t bad_site = 0, bad_at = 0;
 #pragma unroll
         for (int v = 0; v < NV; ++v)
 #pragma unroll
             for (int j = 0; j < VEC; ++j) {
                 const uint32_t bbk = b[v][j] >> 16;
-                if (bbk < (uint32_t)p) {
-                    const uint32_t loc = toff[bbk] + (b[v][j] & 0xFFFFu);
-                    if (loc >= (uint32_t)SUPER) {
-                        flag_bounds(status, 10, loc);
-                        continue;
-                    }
+                const uint32_t loc = toff[min(bbk, (uint32_t)p)] + (b[v][j] & 0xFFFFu);
+                const bool real = bbk < (uint32_t)p, ok = real && loc < (uint32_t)SUPER;
+                if (ok) {
                     sk[loc] = k[v][j];
                     sbk[loc] = (uint16_t)bbk;
                 }
+                if (real && !ok) bad_site = 10, bad_at = loc;
             }
         __syncthreads();
         for (uint32_t jj = threadIdx.x; jj < tvalid; jj += NT) {
-            const uint32_t bbk = sbk[jj];
-            if (bbk >= (uint32_t)p) {          // a slot no key was staged to (after a failed check)
-                flag_bounds(status, 12, jj);
-                continue;
-            }
-            const uint32_t dst = (uint32_t)(delta[bbk] + (int32_t)jj);
-            if (dst >= n) {
-                flag_bounds(status, 11, dst);
-                continue;
-            }
-            out[dst] = sk[jj];
+            const uint32_t bbk = sbk[jj];      // >= p: a slot no key was staged to (after a failed check)
+            const uint32_t dst = (uint32_t)(delta[min(bbk, (uint32_t)p)] + (int32_t)jj);
+            const bool ok = bbk < (uint32_t)p && dst < n;
+            if (ok) out[dst] = sk[jj];
+            if (!ok) bad_site = bbk < (uint32_t)p ? 11u : 12u, bad_at = bbk < (uint32_t)p ? dst : jj;
         }
+        if (bad_site) flag_bounds(status, bad_site, bad_at);
         fence_proxy_async_smem();   // this thread's reads and writes of the buffer before the next copy into it
         __syncthreads();
         if (threadIdx.x == 0 && vec_ok && t + 2 < t1 && whole(t + 2)) {

@@ -626,31 +626,46 @@ k_seg_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restric
             }
             const uint32_t tvalid = block_exclusive_scan(tile_off, p, scratch);
             if (threadIdx.x == 0) tile_off[p] = tvalid;
+            // range checks predicate the accesses; a failed one is reported once
+            // per thread after the write-out (no branch per key)
+            uint32_t bad_site = 0, bad_at = 0;
 #pragma unroll
             for (int i = 0; i < IT; ++i) {
                 const int b = (int)(br[i] >> 16);
-                if (b < p) {
-                    const uint32_t loc = tile_off[b] + (HV ? mycnt[b] : 0u) + (br[i] & 0xFFFFu);
-                    if (loc >= (uint32_t)SUB) {
-                        flag_bounds(status, 10, loc);
-                        continue;
+                if (HV) {
+                    if (b < p) {
+                        const uint32_t loc = tile_off[b] + mycnt[b] + (br[i] & 0xFFFFu);
+                        if (loc >= (uint32_t)SUB) {
+                            flag_bounds(status, 10, loc);
+                            continue;
+                        }
+                        sk[loc] = kv[i];
+                        sv[loc] = vals[r.beg + base + i * 32];
+                        sb[loc] = (uint16_t)b;
                     }
-                    sk[loc] = kv[i];
-                    if (HV) sv[loc] = vals[r.beg + base + i * 32];
-                    sb[loc] = (uint16_t)b;
+                } else {
+                    const uint32_t loc = tile_off[min(b, p)] + (br[i] & 0xFFFFu);
+                    const bool real = b < p, ok = real && loc < (uint32_t)SUB;
+                    if (ok) {
+                        sk[loc] = kv[i];
+                        sb[loc] = (uint16_t)b;
+                    }
+                    if (real && !ok) bad_site = 10, bad_at = loc;
                 }
             }
             __syncthreads();
             for (uint32_t j = threadIdx.x; j < tvalid; j += SNT) {
-                const int b = sb[j];
-                const uint32_t dst = cursor[b] + (j - tile_off[b]);
-                if (dst < r.beg || dst >= seg_end) {
-                    flag_bounds(status, 11, dst);
-                    continue;
+                const int b = sb[j];                       // >= p: a slot no key was staged to
+                const int bc = min(b, p - 1);              // cursor holds p entries
+                const uint32_t dst = cursor[bc] + (j - tile_off[bc]);
+                const bool ok = b < p && dst >= r.beg && dst < seg_end;
+                if (ok) {
+                    out[dst] = sk[j];
+                    if (HV) vout[dst] = sv[j];
                 }
-                out[dst] = sk[j];
-                if (HV) vout[dst] = sv[j];
+                if (!ok) bad_site = 11, bad_at = dst;
             }
+            if (bad_site) flag_bounds(status, bad_site, bad_at);
             __syncthreads();
             for (int b = threadIdx.x; b < p; b += SNT) cursor[b] += tile_off[b + 1] - tile_off[b];
             __syncthreads();
