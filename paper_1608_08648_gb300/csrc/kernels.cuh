@@ -394,7 +394,10 @@ struct LeafSmem {
     static constexpr int IT = LeafCfg<O, HV>::IT;
     static constexpr int CAP = Cap<O>::v;
     static constexpr size_t ex_bytes = (sizeof(E) * padded_len<E>(CAP) + 15) & ~size_t(15);
-    static constexpr size_t bytes = ex_bytes + (HV ? sizeof(uint32_t) * CAP : 0);
+    // 4-byte keys alone: the per-warp key minima and maxima of the narrow test
+    static constexpr bool NARROW = sizeof(O) == 4 && !HV;
+    static constexpr size_t red_bytes = NARROW ? sizeof(uint32_t) * 2 * (NT / 32) : 0;
+    static constexpr size_t bytes = ex_bytes + (HV ? sizeof(uint32_t) * CAP : 0) + red_bytes;
 };
 
 // Sort [beg, beg+len) of `in` (len <= CAP) into the same range of `out`.
@@ -408,16 +411,52 @@ __device__ __forceinline__ void leaf_sort(const typename KT::T* in, const uint32
     constexpr int IT = LS::IT, NT = LS::NT;
     E* ex = reinterpret_cast<E*>(smem);
     uint32_t* sv = reinterpret_cast<uint32_t*>(smem + LS::ex_bytes);
-    for (int j = threadIdx.x; j < (int)len; j += NT) {
-        ex[pad_idx<E>(j)] = LE::make(KT::ord(in[beg + j]), (uint32_t)j);
-        if (HV) sv[j] = vin[beg + j];
-    }
-    __syncthreads();
     E x[IT];
     const int base = threadIdx.x * IT;
+    if constexpr (LS::NARROW) {
+        // A leaf whose keys span at most 2^16 values sorts 16-bit offsets, two a
+        // register (merge_sort_block_narrow); the test needs the key range.
+        uint32_t* red = reinterpret_cast<uint32_t*>(smem + LS::ex_bytes);   // [NT/32] minima, [NT/32] maxima
+        uint32_t kmin = 0xFFFFFFFFu, kmax = 0;
+        for (int j = threadIdx.x; j < (int)len; j += NT) {
+            const E e = LE::make(KT::ord(in[beg + j]), (uint32_t)j);
+            ex[pad_idx<E>(j)] = e;
+            kmin = min(kmin, e.k);
+            kmax = max(kmax, e.k);
+        }
+        kmin = __reduce_min_sync(0xffffffffu, kmin);
+        kmax = __reduce_max_sync(0xffffffffu, kmax);
+        if ((threadIdx.x & 31) == 0) {
+            red[threadIdx.x >> 5] = kmin;
+            red[NT / 32 + (threadIdx.x >> 5)] = kmax;
+        }
+        __syncthreads();
 #pragma unroll
-    for (int i = 0; i < IT; ++i) x[i] = base + i < (int)len ? ex[pad_idx<E>(base + i)] : EMax<E>::v();
-    merge_sort_block<E, NT, IT>(x, ex, (int)len);
+        for (int ww = 0; ww < NT / 32; ++ww) {
+            kmin = min(kmin, red[ww]);
+            kmax = max(kmax, red[NT / 32 + ww]);
+        }
+        const bool narrow = kmax - kmin <= 0xFFFFu && kmin <= 0xFFFF0000u;
+        if (narrow) {
+            narrow_register_sort<IT>(ex, (int)len, kmin);
+#pragma unroll
+            for (int i = 0; i < IT; ++i) x[i] = EMax<E>::v();
+        } else {
+#pragma unroll
+            for (int i = 0; i < IT; ++i) x[i] = base + i < (int)len ? ex[pad_idx<E>(base + i)] : EMax<E>::v();
+            warp_register_sort<E, IT>(x, (int)len);
+        }
+        merge_rounds<E, NT, IT>(x, ex, (int)len, narrow ? 16 * IT : 32 * IT, narrow);
+    } else {
+        for (int j = threadIdx.x; j < (int)len; j += NT) {
+            ex[pad_idx<E>(j)] = LE::make(KT::ord(in[beg + j]), (uint32_t)j);
+            if (HV) sv[j] = vin[beg + j];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < IT; ++i) x[i] = base + i < (int)len ? ex[pad_idx<E>(base + i)] : EMax<E>::v();
+        merge_sort_block<E, NT, IT>(x, ex, (int)len);
+    }
 #pragma unroll
     for (int i = 0; i < IT; ++i)
         if (base + i < (int)len) ex[pad_idx<E>(base + i)] = x[i];

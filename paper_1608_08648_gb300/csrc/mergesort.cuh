@@ -59,6 +59,20 @@ __device__ __forceinline__ E32 emax<E32>(const E32& a, const E32& b) { return E3
 template <>
 __device__ __forceinline__ E64 emax<E64>(const E64& a, const E64& b) { return E64{max(a.k, b.k)}; }
 
+// Two 16-bit keys in one word: the low halves of a thread's words form one set,
+// the high halves another, and one network sorts both sets at once with the
+// SIMD minimum / maximum of unsigned 16-bit halves.
+struct P16 {
+    uint32_t k;
+};
+template <>
+__device__ __forceinline__ void cas_up<P16>(P16& a, P16& b) {
+    uint32_t lo, hi;
+    asm("min.u16x2 %0, %2, %3;\n\tmax.u16x2 %1, %2, %3;" : "=r"(lo), "=r"(hi) : "r"(a.k), "r"(b.k));
+    a.k = lo;
+    b.k = hi;
+}
+
 // Batcher's odd-even merge sort of x[0..IT) ascending (IT a power of two): 191
 // compare-exchanges for 32 elements against 240 for the bitonic network.  The
 // network is unrolled by template recursion so that every index is a
@@ -138,21 +152,29 @@ __device__ __forceinline__ void bitonic_merge_regs(E (&x)[IT]) {
 // registers it later updates), so the shuffles stay next to their compares
 // instead of being hoisted ahead of them, which would hold every shuffled copy
 // of the 32 IT elements live at once.
+#define OSS_XLANE4(TY, S0, S1, S2, S3)                                            \
+    "{\n\t.reg .b32 t0, t1, t2, t3;\n\t.reg .pred pl;\n\t"                       \
+    "setp.ne.u32 pl, %5, 0;\n\t"                                                 \
+    "shfl.sync.bfly.b32 t0, " S0 ", %4, 0x1f, 0xffffffff;\n\t"                    \
+    "shfl.sync.bfly.b32 t1, " S1 ", %4, 0x1f, 0xffffffff;\n\t"                    \
+    "shfl.sync.bfly.b32 t2, " S2 ", %4, 0x1f, 0xffffffff;\n\t"                    \
+    "shfl.sync.bfly.b32 t3, " S3 ", %4, 0x1f, 0xffffffff;\n\t"                    \
+    "@pl min." TY " %0, %0, t0;\n\t"                                             \
+    "@!pl max." TY " %0, %0, t0;\n\t"                                            \
+    "@pl min." TY " %1, %1, t1;\n\t"                                             \
+    "@!pl max." TY " %1, %1, t1;\n\t"                                            \
+    "@pl min." TY " %2, %2, t2;\n\t"                                             \
+    "@!pl max." TY " %2, %2, t2;\n\t"                                            \
+    "@pl min." TY " %3, %3, t3;\n\t"                                             \
+    "@!pl max." TY " %3, %3, t3;\n\t}"
+
 __device__ __forceinline__ void xlane_cas4(E32& a, E32& b, E32& c, E32& d, int dl, uint32_t lower) {
-    asm volatile("{\n\t.reg .u32 t0, t1, t2, t3;\n\t.reg .pred pl;\n\t"
-                 "setp.ne.u32 pl, %5, 0;\n\t"
-                 "shfl.sync.bfly.b32 t0, %0, %4, 0x1f, 0xffffffff;\n\t"
-                 "shfl.sync.bfly.b32 t1, %1, %4, 0x1f, 0xffffffff;\n\t"
-                 "shfl.sync.bfly.b32 t2, %2, %4, 0x1f, 0xffffffff;\n\t"
-                 "shfl.sync.bfly.b32 t3, %3, %4, 0x1f, 0xffffffff;\n\t"
-                 "@pl min.u32 %0, %0, t0;\n\t"
-                 "@!pl max.u32 %0, %0, t0;\n\t"
-                 "@pl min.u32 %1, %1, t1;\n\t"
-                 "@!pl max.u32 %1, %1, t1;\n\t"
-                 "@pl min.u32 %2, %2, t2;\n\t"
-                 "@!pl max.u32 %2, %2, t2;\n\t"
-                 "@pl min.u32 %3, %3, t3;\n\t"
-                 "@!pl max.u32 %3, %3, t3;\n\t}"
+    asm volatile(OSS_XLANE4("u32", "%0", "%1", "%2", "%3")
+                 : "+r"(a.k), "+r"(b.k), "+r"(c.k), "+r"(d.k)
+                 : "r"(dl), "r"(lower));
+}
+__device__ __forceinline__ void xlane_cas4(P16& a, P16& b, P16& c, P16& d, int dl, uint32_t lower) {
+    asm volatile(OSS_XLANE4("u16x2", "%0", "%1", "%2", "%3")
                  : "+r"(a.k), "+r"(b.k), "+r"(c.k), "+r"(d.k)
                  : "r"(dl), "r"(lower));
 }
@@ -161,23 +183,16 @@ __device__ __forceinline__ void xlane_cas4(E32& a, E32& b, E32& c, E32& d, int d
 // (c, d) = (x[k+1], x[IT-2-k]): a meets the partner's b, b the partner's a, and
 // so on, partner = lane ^ m.
 __device__ __forceinline__ void xlane_mirror4(E32& a, E32& b, E32& c, E32& d, int m, uint32_t lower) {
-    asm volatile("{\n\t.reg .u32 t0, t1, t2, t3;\n\t.reg .pred pl;\n\t"
-                 "setp.ne.u32 pl, %5, 0;\n\t"
-                 "shfl.sync.bfly.b32 t0, %1, %4, 0x1f, 0xffffffff;\n\t"
-                 "shfl.sync.bfly.b32 t1, %0, %4, 0x1f, 0xffffffff;\n\t"
-                 "shfl.sync.bfly.b32 t2, %3, %4, 0x1f, 0xffffffff;\n\t"
-                 "shfl.sync.bfly.b32 t3, %2, %4, 0x1f, 0xffffffff;\n\t"
-                 "@pl min.u32 %0, %0, t0;\n\t"
-                 "@!pl max.u32 %0, %0, t0;\n\t"
-                 "@pl min.u32 %1, %1, t1;\n\t"
-                 "@!pl max.u32 %1, %1, t1;\n\t"
-                 "@pl min.u32 %2, %2, t2;\n\t"
-                 "@!pl max.u32 %2, %2, t2;\n\t"
-                 "@pl min.u32 %3, %3, t3;\n\t"
-                 "@!pl max.u32 %3, %3, t3;\n\t}"
+    asm volatile(OSS_XLANE4("u32", "%1", "%0", "%3", "%2")
                  : "+r"(a.k), "+r"(b.k), "+r"(c.k), "+r"(d.k)
                  : "r"(m), "r"(lower));
 }
+__device__ __forceinline__ void xlane_mirror4(P16& a, P16& b, P16& c, P16& d, int m, uint32_t lower) {
+    asm volatile(OSS_XLANE4("u16x2", "%1", "%0", "%3", "%2")
+                 : "+r"(a.k), "+r"(b.k), "+r"(c.k), "+r"(d.k)
+                 : "r"(m), "r"(lower));
+}
+#undef OSS_XLANE4
 
 template <class E, int IT>
 __device__ __forceinline__ void warp_bitonic_level(E (&x)[IT], int v) {
@@ -202,6 +217,103 @@ __device__ __forceinline__ void warp_bitonic_levels(E (&x)[IT], int levels) {
     for (int v = 0; v < levels; ++v) warp_bitonic_level<E, IT>(x, v);
 }
 
+// One merge round: the thread's IT outputs (diagonal d of its pair, the pair of
+// runs of length `run` starting at pb) from the runs in sk, which spans
+// padded_len<E>(NT IT) elements with 2 run <= NT IT.
+template <class E, int IT>
+__device__ __forceinline__ void merge_pair(E (&x)[IT], const E* sk, int base, int run) {
+    const int pb = base & ~(2 * run - 1);      // first position of the pair
+    const int d = base - pb;                   // output diagonal inside the pair
+    const E* A = sk;                           // A[j] = sk[pb + j]
+    int lo = max(0, d - run), hi = min(d, run);
+    while (lo < hi) {                          // left-run outputs among the first d
+        const int mid = (lo + hi) >> 1;
+        const E av = A[pad_idx<E>(pb + mid)];
+        const E bv = A[pad_idx<E>(pb + run + d - 1 - mid)];
+        if (E::lt(bv, av)) hi = mid;
+        else lo = mid + 1;
+    }
+    if constexpr (sizeof(E) <= 8) {
+        // Serial merge of the thread's IT outputs: the heads of both runs in
+        // registers, one shared load per output to refill the consumed side
+        // (ties go to the left run).  The loads are unconditional: a run's end
+        // reads at most position pb + 2 run <= NT IT, inside the padded buffer,
+        // and the value read there is replaced by +infinity (no branch).
+        int ia = lo, ib = d - lo;
+        const E a0 = A[pad_idx<E>(pb + ia)], b0 = A[pad_idx<E>(pb + run + ib)];
+        E av = ia < run ? a0 : EMax<E>::v();
+        E bv = ib < run ? b0 : EMax<E>::v();
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const bool take_b = E::lt(bv, av);
+            x[i] = take_b ? bv : av;
+            if (i + 1 < IT) {
+                const int nx = take_b ? ib + 1 : ia + 1;
+                const int nidx = take_b ? pb + run + nx : pb + nx;
+                const E nl = A[pad_idx<E>(nidx)];
+                const E nv = nx < run ? nl : EMax<E>::v();
+                ia += take_b ? 0 : 1;
+                ib += take_b ? 1 : 0;
+                av = take_b ? av : nv;
+                bv = take_b ? nv : bv;
+            }
+        }
+    } else {
+        // (key, position) triples: the IT smallest of A[ai, ai+IT) and
+        // B[bi, bi+IT) as min(A[ai+i], B[bi+IT-1-i]) (a bitonic sequence,
+        // the half-cleaner of a bitonic merge), sorted by log2(IT) register
+        // stages; fewer live registers than the serial merge of triples.
+        const int ai = lo, bi = d - lo;
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const int ia = ai + i, ib = bi + IT - 1 - i;
+            const E av = ia < run ? A[pad_idx<E>(pb + ia)] : EMax<E>::v();
+            const E bv = ib < run ? A[pad_idx<E>(pb + run + ib)] : EMax<E>::v();
+            x[i] = emin(av, bv);
+        }
+        bitonic_merge_regs<E, IT>(x);
+    }
+}
+
+// The merge rounds from sorted runs of `run` (thread-blocked in x, or already
+// in sk when in_smem) up to len; a round whose runs are in sk runs even when
+// run >= len.  Ends with __syncthreads.  Callers share this one copy of the
+// unrolled merge (its code is large; copies of it cost instruction fetches).
+template <class E, int NT, int IT>
+__device__ __forceinline__ void merge_rounds(E (&x)[IT], E* sk, int len, int run, bool in_smem) {
+    const int base = threadIdx.x * IT;
+    const bool active = base < len;
+    for (; run < len || in_smem; run *= 2) {
+        // A pair of runs that fits in one warp's elements is merged by that warp
+        // alone, so only the larger rounds need the whole block.
+        const bool block_wide = 2 * run > 32 * IT;
+        if (!in_smem) {
+            if (block_wide) __syncthreads();
+            else __syncwarp();
+#pragma unroll
+            for (int i = 0; i < IT; ++i) sk[pad_idx<E>(base + i)] = x[i];   // beyond len: +infinity
+        }
+        in_smem = false;
+        if (block_wide) __syncthreads();
+        else __syncwarp();
+        if (active) merge_pair<E, IT>(x, sk, base, run);
+    }
+    __syncthreads();
+}
+
+// Sorts each warp's 32 IT single-word elements in registers: every lane its IT
+// (Batcher), then the warp's lanes together (bitonic levels), as far as the
+// first min(len, 32 IT) elements need.  Padding lanes take part (the shuffles
+// need the whole warp).
+template <class E, int IT>
+__device__ __forceinline__ void warp_register_sort(E (&x)[IT], int len) {
+    oddeven_sort_regs<E, IT>(x);
+    const int wlen = min(len, 32 * IT);     // elements the warps must order among themselves
+    int levels = 0;
+    while ((IT << levels) < wlen) ++levels;
+    warp_bitonic_levels<E, IT>(x, levels);
+}
+
 // x: the thread's IT elements at positions tid*IT + i (blocked; positions >= len
 // must hold EMax).  sk: shared memory for padded_len<E>(NT*IT) elements; the
 // whole block must hold NT*IT >= len.  On
@@ -217,12 +329,7 @@ __device__ __forceinline__ void merge_sort_block(E (&x)[IT], E* sk, int len) {
     const bool active = base < len;
     int run0 = IT;
     if constexpr (sizeof(E) == 4) {
-        // every lane sorts (padding included: the shuffles need the whole warp)
-        oddeven_sort_regs<E, IT>(x);
-        const int wlen = min(len, 32 * IT);     // elements the warps must order among themselves
-        int levels = 0;
-        while ((IT << levels) < wlen) ++levels;
-        warp_bitonic_levels<E, IT>(x, levels);
+        warp_register_sort<E, IT>(x, len);
         run0 = 32 * IT;
     } else if (active) {
         // (key, position) triples keep the bitonic network: its shorter live
@@ -230,67 +337,41 @@ __device__ __forceinline__ void merge_sort_block(E (&x)[IT], E* sk, int len) {
         if constexpr (sizeof(E) <= 8) oddeven_sort_regs<E, IT>(x);
         else bitonic_sort_regs<E, IT>(x);
     }
-    for (int run = run0; run < len; run *= 2) {
-        // A pair of runs that fits in one warp's elements is merged by that warp
-        // alone, so only the larger rounds need the whole block.
-        const bool block_wide = 2 * run > 32 * IT;
-        if (block_wide) __syncthreads();
-        else __syncwarp();
+    merge_rounds<E, NT, IT>(x, sk, len, run0, false);
+}
+
+// The register phase for single-word elements sk[pad_idx(j)], j < len, all
+// within 0xFFFF of kmin (kmin <= 0xFFFF0000): a leaf whose keys span at most
+// 2^16 values.  Each thread packs its IT elements as IT/2 words of two 16-bit
+// offsets from kmin (padding: 0xFFFF, which unpacks to kmin + 0xFFFF, no
+// smaller than any element); one register network sorts the low-half set and
+// the high-half set of every warp (IT/2 a lane, then across the warp), half the
+// instructions per element of the 32-bit network.  The two sets of each warp go
+// back to sk, unpacked, as two adjacent runs of 16 IT: merge_rounds with
+// run = 16 IT and in_smem merges them and carries on.  A warp reads and writes
+// only its own 32 IT positions; ends with __syncwarp.
+template <int IT>
+__device__ __forceinline__ void narrow_register_sort(E32* sk, int len, uint32_t kmin) {
+    constexpr int H = IT / 2;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int base = threadIdx.x * IT;
+    P16 y[H];
 #pragma unroll
-        for (int i = 0; i < IT; ++i) sk[pad_idx<E>(base + i)] = x[i];   // beyond len: +infinity
-        if (block_wide) __syncthreads();
-        else __syncwarp();
-        if (active) {
-            const int pb = base & ~(2 * run - 1);      // first position of the pair
-            const int d = base - pb;                   // output diagonal inside the pair
-            const E* A = sk;                           // A[j] = sk[pb + j]
-            int lo = max(0, d - run), hi = min(d, run);
-            while (lo < hi) {                          // left-run outputs among the first d
-                const int mid = (lo + hi) >> 1;
-                const E av = A[pad_idx<E>(pb + mid)];
-                const E bv = A[pad_idx<E>(pb + run + d - 1 - mid)];
-                if (E::lt(bv, av)) hi = mid;
-                else lo = mid + 1;
-            }
-            if constexpr (sizeof(E) <= 8) {
-                // Serial merge of the thread's IT outputs: the heads of both runs in
-                // registers, one shared load per output to refill the consumed side
-                // (ties go to the left run).
-                int ia = lo, ib = d - lo;
-                E av = ia < run ? A[pad_idx<E>(pb + ia)] : EMax<E>::v();
-                E bv = ib < run ? A[pad_idx<E>(pb + run + ib)] : EMax<E>::v();
-#pragma unroll
-                for (int i = 0; i < IT; ++i) {
-                    const bool take_b = E::lt(bv, av);
-                    x[i] = take_b ? bv : av;
-                    if (i + 1 < IT) {
-                        const int nx = take_b ? ib + 1 : ia + 1;
-                        const int nidx = take_b ? pb + run + nx : pb + nx;
-                        const E nv = nx < run ? A[pad_idx<E>(nidx)] : EMax<E>::v();
-                        ia += take_b ? 0 : 1;
-                        ib += take_b ? 1 : 0;
-                        av = take_b ? av : nv;
-                        bv = take_b ? nv : bv;
-                    }
-                }
-            } else {
-                // (key, position) triples: the IT smallest of A[ai, ai+IT) and
-                // B[bi, bi+IT) as min(A[ai+i], B[bi+IT-1-i]) (a bitonic sequence,
-                // the half-cleaner of a bitonic merge), sorted by log2(IT) register
-                // stages; fewer live registers than the serial merge of triples.
-                const int ai = lo, bi = d - lo;
-#pragma unroll
-                for (int i = 0; i < IT; ++i) {
-                    const int ia = ai + i, ib = bi + IT - 1 - i;
-                    const E av = ia < run ? A[pad_idx<E>(pb + ia)] : EMax<E>::v();
-                    const E bv = ib < run ? A[pad_idx<E>(pb + run + ib)] : EMax<E>::v();
-                    x[i] = emin(av, bv);
-                }
-                bitonic_merge_regs<E, IT>(x);
-            }
-        }
+    for (int r = 0; r < H; ++r) {
+        const int j0 = base + 2 * r, j1 = j0 + 1;
+        const uint32_t o0 = j0 < len ? sk[pad_idx<E32>(j0)].k - kmin : 0xFFFFu;
+        const uint32_t o1 = j1 < len ? sk[pad_idx<E32>(j1)].k - kmin : 0xFFFFu;
+        y[r].k = o0 | (o1 << 16);
     }
-    __syncthreads();
+    warp_register_sort<P16, H>(y, (len + 1) / 2);   // lanes of 2 H positions: as for IT positions
+    __syncwarp();                               // the warp's lanes have read their input
+    const int lo0 = w * 32 * IT + lane * H, hi0 = lo0 + 16 * IT;
+#pragma unroll
+    for (int r = 0; r < H; ++r) {
+        sk[pad_idx<E32>(lo0 + r)] = E32{kmin + (y[r].k & 0xFFFFu)};
+        sk[pad_idx<E32>(hi0 + r)] = E32{kmin + (y[r].k >> 16)};
+    }
+    __syncwarp();
 }
 
 }  // namespace ossort

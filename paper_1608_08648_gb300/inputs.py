@@ -158,6 +158,14 @@ def int_keys(dist: str, n: int, seed: int, p: int, start: int = 0, count: int | 
     raise ValueError(f"unknown distribution {dist!r}")
 
 
+def narrow_i32_keys(n: int, lo: int, width: int, seed: int = 1, start: int = 0, count: int | None = None,
+                    device="cpu") -> torch.Tensor:
+    """int32 keys uniform in [lo, lo + width) (lo + width <= 2^31): inputs whose
+    buckets span few distinct values."""
+    i = _positions(n, start, count, device)
+    return (lo + _v31(seed, S_UNIFORM, i) % width).to(torch.int32)
+
+
 def keys(dist: str, n: int, dtype: str, seed: int = 1, p: int = 1024, start: int = 0,
          count: int | None = None, device="cpu") -> torch.Tensor:
     """Keys of type ``dtype`` in {'i32', 'u64', 'f64'} for a named distribution.

@@ -182,3 +182,18 @@ def test_keys_not_16_byte_aligned(kt, shift):
         assert np.array_equal(to_np(ko, kt).view(np.uint8), ref["keys"].view(np.uint8)), f"{split}: keys differ"
         assert np.array_equal(st["bucket_sizes"], ref["bucket_sizes"])
         assert np.array_equal(st["spl_tags"], ref["spl_tags"])
+
+
+@pytest.mark.parametrize("lo,width", [(0, 1 << 16), (-(1 << 31), 1 << 12), ((1 << 31) - (1 << 17), 1 << 17),
+                                      (12345, 1 << 22), (-(1 << 20), 1 << 21)])
+def test_narrow_range_leaves(lo, width):
+    """Keys from a narrow range: leaves whose keys span at most 2^16 values sort
+    16-bit offsets two to a register, wider ones the 32-bit elements; the cases
+    mix both, put keys next to either end of the int32 range (offsets from a
+    minimum close to the top stay on the 32-bit path) and include many equal
+    keys."""
+    for n, p, s in (((1 << 20) + 333, 64, 8), (300007, 16, 3), (8193, 4, 2), (4097, 4, 2), (100, 4, 2)):
+        keys = inputs.narrow_i32_keys(n, lo, width, seed=n).numpy()
+        check(keys, "i32", "ran", p, s, seed=n, with_vals=False)
+        check(keys, "i32", "det", p, s, seed=n, with_vals=False)
+        check(keys, "i32", "ran", p, s, seed=n)

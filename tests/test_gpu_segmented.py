@@ -88,6 +88,20 @@ def test_mixed_batch_matches_oracle(kt, table, dist, with_vals):
     check_against_oracle(kt, classes, seed, *res)
 
 
+def test_narrow_int32_segments():
+    """int32 segments whose leaves span at most 2^16 values (the packed 16-bit
+    leaf sort, also on whole segments sorted directly by the leaf kernel)."""
+    kt = "i32"
+    classes = TABLES["whole_up_to_3cap"](CAP[kt])
+    lengths = mixed_lengths(kt, seed=13)
+    off = inputs.segment_offsets(torch.tensor(lengths, dtype=torch.int64))
+    n = int(off[-1])
+    keys = inputs.narrow_i32_keys(n, -(1 << 15), 1 << 16, seed=5, device="cuda")
+    out, _, st = oss.sort_segmented(keys, off.cuda(), classes=classes, seed=5, key_type=kt, stats=True)
+    torch.cuda.synchronize()
+    check_against_oracle(kt, classes, 5, off, keys, None, out, None, st)
+
+
 def test_edge_f64_values_and_single_segment():
     # signed zeros, infinities and subnormals, in one segment and split in many
     n = 200_003
