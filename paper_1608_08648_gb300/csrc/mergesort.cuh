@@ -217,23 +217,82 @@ __device__ __forceinline__ void warp_bitonic_levels(E (&x)[IT], int levels) {
     for (int v = 0; v < levels; ++v) warp_bitonic_level<E, IT>(x, v);
 }
 
+// Layout of the runs in sk during the merge rounds.  4-byte elements (IT a
+// multiple of the 32-element padding group) keep the second run of every pair
+// descending, so that a pair is one bitonic sequence (up, then down): the
+// smallest element not yet output always sits at one of the two ends of the
+// part not yet output, and the serial merge takes the smaller end with no
+// end-of-run test.  Other elements keep both runs ascending (measured: 8-byte
+// elements, 16 a thread, lose more to the half-warp branch of the reversed
+// stores in the warp-level rounds than the merge saves).
+template <class E, int IT> struct MergeRev {
+    static constexpr bool v = sizeof(E) == 4 && IT % 32 == 0;
+};
+
+// Store the thread's IT sorted elements (positions base .. base+IT-1 of the
+// block's sequence) as the runs of length `run` that the next round merges.
+template <class E, int IT>
+__device__ __forceinline__ void store_run(const E (&x)[IT], E* sk, int base, int run) {
+    if constexpr (MergeRev<E, IT>::v) {
+        const int pb = base & ~(2 * run - 1);
+        if (base - pb >= run) {
+            // second run of its pair, descending: position q goes to 2 pb + 3 run - 1 - q;
+            // mb is a multiple of the padding group, so pad_idx splits into a
+            // register part and a constant part
+            const int mb = 2 * pb + 3 * run - base - IT;
+            E* s0 = sk + pad_idx<E>(mb);
+#pragma unroll
+            for (int i = 0; i < IT; ++i) s0[pad_idx<E>(IT - 1 - i)] = x[i];
+            return;
+        }
+        E* s0 = sk + pad_idx<E>(base);
+#pragma unroll
+        for (int i = 0; i < IT; ++i) s0[pad_idx<E>(i)] = x[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < IT; ++i) sk[pad_idx<E>(base + i)] = x[i];
+    }
+}
+
 // One merge round: the thread's IT outputs (diagonal d of its pair, the pair of
-// runs of length `run` starting at pb) from the runs in sk, which spans
-// padded_len<E>(NT IT) elements with 2 run <= NT IT.
+// runs of length `run` starting at pb) from the runs in sk, laid out as
+// store_run leaves them.  sk spans padded_len<E>(NT IT) elements, 2 run <= NT IT.
 template <class E, int IT>
 __device__ __forceinline__ void merge_pair(E (&x)[IT], const E* sk, int base, int run) {
     const int pb = base & ~(2 * run - 1);      // first position of the pair
     const int d = base - pb;                   // output diagonal inside the pair
     const E* A = sk;                           // A[j] = sk[pb + j]
+    constexpr bool REV = MergeRev<E, IT>::v;
+    // ascending element k of the second run sits at pb + run + k, or (descending
+    // layout) at pb + 2 run - 1 - k
     int lo = max(0, d - run), hi = min(d, run);
     while (lo < hi) {                          // left-run outputs among the first d
         const int mid = (lo + hi) >> 1;
         const E av = A[pad_idx<E>(pb + mid)];
-        const E bv = A[pad_idx<E>(pb + run + d - 1 - mid)];
+        const E bv = A[pad_idx<E>(REV ? pb + 2 * run - d + mid : pb + run + d - 1 - mid)];
         if (E::lt(bv, av)) hi = mid;
         else lo = mid + 1;
     }
-    if constexpr (sizeof(E) <= 8) {
+    if constexpr (REV) {
+        // Serial merge over the bitonic pair: the part not yet output is
+        // [i, j]; its smallest element is sk[i] or sk[j]; one shared load per
+        // output refills the consumed end.  While outputs remain, some element
+        // remains, so i <= j and every load stays inside the pair.
+        int i = pb + lo, j = pb + 2 * run - 1 - (d - lo);
+        E si = A[pad_idx<E>(i)], sj = A[pad_idx<E>(j)];
+#pragma unroll
+        for (int k = 0; k < IT; ++k) {
+            const bool tj = E::lt(sj, si);
+            x[k] = tj ? sj : si;
+            if (k + 1 < IT) {
+                i += tj ? 0 : 1;
+                j -= tj ? 1 : 0;
+                const E nl = A[pad_idx<E>(tj ? j : i)];
+                si = tj ? si : nl;
+                sj = tj ? nl : sj;
+            }
+        }
+    } else if constexpr (sizeof(E) <= 8) {
         // Serial merge of the thread's IT outputs: the heads of both runs in
         // registers, one shared load per output to refill the consumed side
         // (ties go to the left run).  The loads are unconditional: a run's end
@@ -244,10 +303,10 @@ __device__ __forceinline__ void merge_pair(E (&x)[IT], const E* sk, int base, in
         E av = ia < run ? a0 : EMax<E>::v();
         E bv = ib < run ? b0 : EMax<E>::v();
 #pragma unroll
-        for (int i = 0; i < IT; ++i) {
+        for (int k = 0; k < IT; ++k) {
             const bool take_b = E::lt(bv, av);
-            x[i] = take_b ? bv : av;
-            if (i + 1 < IT) {
+            x[k] = take_b ? bv : av;
+            if (k + 1 < IT) {
                 const int nx = take_b ? ib + 1 : ia + 1;
                 const int nidx = take_b ? pb + run + nx : pb + nx;
                 const E nl = A[pad_idx<E>(nidx)];
@@ -265,20 +324,21 @@ __device__ __forceinline__ void merge_pair(E (&x)[IT], const E* sk, int base, in
         // stages; fewer live registers than the serial merge of triples.
         const int ai = lo, bi = d - lo;
 #pragma unroll
-        for (int i = 0; i < IT; ++i) {
-            const int ia = ai + i, ib = bi + IT - 1 - i;
+        for (int k = 0; k < IT; ++k) {
+            const int ia = ai + k, ib = bi + IT - 1 - k;
             const E av = ia < run ? A[pad_idx<E>(pb + ia)] : EMax<E>::v();
             const E bv = ib < run ? A[pad_idx<E>(pb + run + ib)] : EMax<E>::v();
-            x[i] = emin(av, bv);
+            x[k] = emin(av, bv);
         }
         bitonic_merge_regs<E, IT>(x);
     }
 }
 
 // The merge rounds from sorted runs of `run` (thread-blocked in x, or already
-// in sk when in_smem) up to len; a round whose runs are in sk runs even when
-// run >= len.  Ends with __syncthreads.  Callers share this one copy of the
-// unrolled merge (its code is large; copies of it cost instruction fetches).
+// in sk as store_run leaves them when in_smem) up to len; a round whose runs are
+// in sk runs even when run >= len.  Ends with __syncthreads.  Callers share
+// this one copy of the unrolled merge (its code is large; copies of it cost
+// instruction fetches).
 template <class E, int NT, int IT>
 __device__ __forceinline__ void merge_rounds(E (&x)[IT], E* sk, int len, int run, bool in_smem) {
     const int base = threadIdx.x * IT;
@@ -290,8 +350,7 @@ __device__ __forceinline__ void merge_rounds(E (&x)[IT], E* sk, int len, int run
         if (!in_smem) {
             if (block_wide) __syncthreads();
             else __syncwarp();
-#pragma unroll
-            for (int i = 0; i < IT; ++i) sk[pad_idx<E>(base + i)] = x[i];   // beyond len: +infinity
+            store_run<E, IT>(x, sk, base, run);     // beyond len: +infinity
         }
         in_smem = false;
         if (block_wide) __syncthreads();
@@ -347,8 +406,9 @@ __device__ __forceinline__ void merge_sort_block(E (&x)[IT], E* sk, int len) {
 // smaller than any element); one register network sorts the low-half set and
 // the high-half set of every warp (IT/2 a lane, then across the warp), half the
 // instructions per element of the 32-bit network.  The two sets of each warp go
-// back to sk, unpacked, as two adjacent runs of 16 IT: merge_rounds with
-// run = 16 IT and in_smem merges them and carries on.  A warp reads and writes
+// back to sk, unpacked, as the two runs of 16 IT of one pair (the second
+// descending, as store_run lays it out): merge_rounds with run = 16 IT and
+// in_smem merges them and carries on.  A warp reads and writes
 // only its own 32 IT positions; ends with __syncwarp.
 template <int IT>
 __device__ __forceinline__ void narrow_register_sort(E32* sk, int len, uint32_t kmin) {
@@ -365,11 +425,15 @@ __device__ __forceinline__ void narrow_register_sort(E32* sk, int len, uint32_t 
     }
     warp_register_sort<P16, H>(y, (len + 1) / 2);   // lanes of 2 H positions: as for IT positions
     __syncwarp();                               // the warp's lanes have read their input
-    const int lo0 = w * 32 * IT + lane * H, hi0 = lo0 + 16 * IT;
+    // low set ascending at w 32 IT + 32 lane + r, high set descending (the
+    // layout store_run gives the second run of a pair) from the warp's end
+    static_assert(H % 32 == 0, "lane blocks of whole padding groups");
+    E32* lo0 = sk + pad_idx<E32>(w * 32 * IT + lane * H);
+    E32* hi0 = sk + pad_idx<E32>(w * 32 * IT + 32 * IT - H - lane * H);
 #pragma unroll
     for (int r = 0; r < H; ++r) {
-        sk[pad_idx<E32>(lo0 + r)] = E32{kmin + (y[r].k & 0xFFFFu)};
-        sk[pad_idx<E32>(hi0 + r)] = E32{kmin + (y[r].k >> 16)};
+        lo0[pad_idx<E32>(r)] = E32{kmin + (y[r].k & 0xFFFFu)};
+        hi0[pad_idx<E32>(H - 1 - r)] = E32{kmin + (y[r].k >> 16)};
     }
     __syncwarp();
 }
