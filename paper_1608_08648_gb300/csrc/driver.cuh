@@ -315,10 +315,10 @@ size_t classify_smem(int p, int lbits) {
     return split_table_bytes<typename KT::O>(p - 1, lbits) + sizeof(uint32_t) * (p + 1);
 }
 
-template <class KT, bool HV>
+template <class KT, bool HV, bool WIDE = false>
 size_t scatter_smem(int p) {
     using T = typename KT::T;
-    using SC = ScatterCfg<T, HV>;
+    using SC = ScatterCfg<T, HV, WIDE>;
     constexpr int SUB = SC::SUB;
     size_t b = sizeof(T) * SUB + (HV ? sizeof(uint32_t) * SUB : 0);
     b += sizeof(uint32_t) * (p + 1) + sizeof(uint32_t) * p + sizeof(uint32_t) * 32;
@@ -408,36 +408,53 @@ void partition_top_v(Ctx& c, const typename KT::T* src, uint32_t n, const typena
     }
 }
 
-template <class KT, bool HV>
-void partition_top(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, uint32_t n,
-                   const typename KT::O* spl_o, const uint32_t* spl_t, uint32_t p, typename KT::T* dst,
-                   uint32_t* vdst, uint32_t* boff, uint32_t* bsize) {
-    if constexpr (!HV) {
-        partition_top_v<KT>(c, src, n, spl_o, spl_t, p, dst, boff, bsize);
-        return;
-    }
+template <class KT, bool HV, bool WIDE>
+void partition_top_cfg(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, uint32_t n,
+                       const typename KT::O* spl_o, const uint32_t* spl_t, uint32_t p, typename KT::T* dst,
+                       uint32_t* vdst, uint32_t* boff, uint32_t* bsize) {
+    using SC = ScatterCfg<typename KT::T, HV, WIDE>;
     const int lb = table_lbits(p);
-    constexpr uint32_t SUPER = ScatterCfg<typename KT::T, HV>::SUPER;
+    constexpr uint32_t SUPER = SC::SUPER;
     const uint32_t ntiles = (n + SUPER - 1) / SUPER;
     const uint32_t gmax = std::min<uint32_t>(std::max<uint32_t>(ntiles, 1), G_CAP);
     uint32_t* hist = c.ar.take<uint32_t>((size_t)p * gmax);
     uint32_t* col = c.ar.take<uint32_t>((size_t)p * gmax);
     uint16_t* bid = c.ar.take<uint16_t>(n);
     if (!c.live()) return;
-    constexpr int NTS = ScatterCfg<typename KT::T, HV>::NT;
-    const size_t sm_c = classify_smem<KT>(p, lb), sm_s = scatter_smem<KT, HV>(p);
-    smem_at_least(reinterpret_cast<const void*>(k_classify<KT, HV>), sm_c);
-    smem_at_least(reinterpret_cast<const void*>(k_scatter<KT, HV>), sm_s);
-    const int occ = occupancy(k_scatter<KT, HV>, NTS, sm_s);
+    constexpr int NTS = SC::NT;
+    auto kc = k_classify<KT, HV, WIDE>;
+    auto ks = k_scatter<KT, HV, WIDE>;
+    const size_t sm_c = classify_smem<KT>(p, lb), sm_s = scatter_smem<KT, HV, WIDE>(p);
+    smem_at_least(reinterpret_cast<const void*>(kc), sm_c);
+    smem_at_least(reinterpret_cast<const void*>(ks), sm_s);
+    const int occ = occupancy(ks, NTS, sm_s);
     const uint32_t G = std::max<uint32_t>(1, std::min<uint32_t>(gmax, (uint32_t)(c.num_sms * occ)));
     OS_LAUNCH(c.st, c.nested ? "k_classify.sample" : "k_classify",
-              k_classify<KT, HV><<<G, NTS, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, lb, hist, bid, ntiles));
+              kc<<<G, NTS, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, lb, hist, bid, ntiles));
     OS_LAUNCH(c.st, c.nested ? "k_column_scan.sample" : "k_column_scan",
               k_column_scan<<<grid_for((uint64_t)p * 32, 256), 256, 0, c.st>>>(hist, p, G, col, bsize));
     OS_LAUNCH(c.st, c.nested ? "k_bucket_offsets.sample" : "k_bucket_offsets", k_bucket_offsets<<<1, 1024, 0, c.st>>>(bsize, p, boff));
     OS_LAUNCH(c.st, c.nested ? "k_scatter.sample" : "k_scatter",
-              k_scatter<KT, HV><<<G, NTS, sm_s, c.st>>>(src, vsrc, bid, n, (int)p, col, boff, dst, vdst,
-                                                           ntiles, c.status));
+              ks<<<G, NTS, sm_s, c.st>>>(src, vsrc, bid, n, (int)p, col, boff, dst, vdst, ntiles, c.status));
+}
+
+// Keys alone take the vector passes; payload sorts the stable pair above, with
+// the WIDE configuration for 4-byte keys while p <= HV_WIDE_MAX_P (a choice on
+// p alone, so that the workspace plan and the launches agree).
+template <class KT, bool HV>
+void partition_top(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, uint32_t n,
+                   const typename KT::O* spl_o, const uint32_t* spl_t, uint32_t p, typename KT::T* dst,
+                   uint32_t* vdst, uint32_t* boff, uint32_t* bsize) {
+    if constexpr (!HV) {
+        partition_top_v<KT>(c, src, n, spl_o, spl_t, p, dst, boff, bsize);
+    } else if constexpr (sizeof(typename KT::T) == 4) {
+        if (p <= (uint32_t)HV_WIDE_MAX_P)
+            partition_top_cfg<KT, HV, true>(c, src, vsrc, n, spl_o, spl_t, p, dst, vdst, boff, bsize);
+        else
+            partition_top_cfg<KT, HV, false>(c, src, vsrc, n, spl_o, spl_t, p, dst, vdst, boff, bsize);
+    } else {
+        partition_top_cfg<KT, HV, false>(c, src, vsrc, n, spl_o, spl_t, p, dst, vdst, boff, bsize);
+    }
 }
 
 template <class KT, bool HV>

@@ -130,15 +130,15 @@ __host__ __device__ inline uint32_t tile_lo(uint32_t g, uint32_t G, uint32_t nti
     return (uint32_t)(((uint64_t)g * ntiles) / G);
 }
 
-template <class KT, bool HV>
-__global__ void __launch_bounds__(ScatterCfg<typename KT::T, HV>::NT,
-                                  ScatterCfg<typename KT::T, HV>::NT >= 1024 ? 1
-                                  : (ScatterCfg<typename KT::T, HV>::NT == 512 ? 2 : 3))
+template <class KT, bool HV, bool WIDE = false>
+__global__ void __launch_bounds__(ScatterCfg<typename KT::T, HV, WIDE>::NT,
+                                  ScatterCfg<typename KT::T, HV, WIDE>::NT >= 1024 ? 1
+                                  : (ScatterCfg<typename KT::T, HV, WIDE>::NT == 512 ? 2 : 3))
 k_classify(const typename KT::T* __restrict__ keys, uint32_t n, const typename KT::O* __restrict__ spl_o,
            const uint32_t* __restrict__ spl_t, int p, int lbits, uint32_t* __restrict__ hist,
            uint16_t* __restrict__ bid, uint32_t ntiles) {
     using O = typename KT::O;
-    constexpr int NT = ScatterCfg<typename KT::T, HV>::NT, SUPER = ScatterCfg<typename KT::T, HV>::SUPER;
+    constexpr int NT = ScatterCfg<typename KT::T, HV, WIDE>::NT, SUPER = ScatterCfg<typename KT::T, HV, WIDE>::SUPER;
     extern __shared__ __align__(16) char smem[];
     SplitTable<O> tb;
     tb.bind(smem, p - 1, lbits);
@@ -223,16 +223,18 @@ static __global__ void k_bucket_offsets(const uint32_t* __restrict__ bsize, uint
 // alone need no order inside a bucket (equal keys are identical), so
 // shared-memory atomics, one per run of equal neighbours, hand out the slots.
 // ---------------------------------------------------------------------------
-template <class KT, bool HV>
-__global__ void __launch_bounds__(ScatterCfg<typename KT::T, HV>::NT, ScatterCfg<typename KT::T, HV>::NT >= 1024 ? 1
-                                  : ScatterCfg<typename KT::T, HV>::NT == 512 ? 2
+template <class KT, bool HV, bool WIDE = false>
+__global__ void __launch_bounds__(ScatterCfg<typename KT::T, HV, WIDE>::NT,
+                                  ScatterCfg<typename KT::T, HV, WIDE>::NT >= 1024 ? 1
+                                  : ScatterCfg<typename KT::T, HV, WIDE>::NT == 512 ? 2
                                   : (sizeof(typename KT::T) == 4 ? 4 : 3))
 k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ vals,
           const uint16_t* __restrict__ bid, uint32_t n, int p, const uint32_t* __restrict__ col,
           const uint32_t* __restrict__ boff, typename KT::T* __restrict__ out, uint32_t* __restrict__ vout,
           uint32_t ntiles, uint32_t* status) {
     using T = typename KT::T;
-    using SC = ScatterCfg<typename KT::T, HV>;
+    using SC = ScatterCfg<typename KT::T, HV, WIDE>;
+    constexpr bool PF = HV && SC::PREFETCH;
     constexpr int SNT = SC::NT, SWARPS = SC::WARPS, SUB = SC::SUB, SUPER = SC::SUPER;
     extern __shared__ __align__(16) char smem[];
     char* q = smem;
@@ -256,11 +258,13 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
         const uint32_t base = tbase + w * (TOP_IT * 32) + lane;
         T kv[TOP_IT];
         uint32_t br[TOP_IT];   // bucket << 16 | rank inside the tile's part of the bucket
+        uint32_t vv[PF ? TOP_IT : 1];
 #pragma unroll
         for (int i = 0; i < TOP_IT; ++i) {
             const uint32_t e = base + i * 32;
             kv[i] = e < n ? keys[e] : T(0);
             br[i] = e < n ? (uint32_t)bid[e] : (uint32_t)p;
+            if constexpr (PF) vv[i] = e < n ? vals[e] : 0u;
         }
         if (HV) {
             for (int b = lane; b <= p; b += 32) mycnt[b] = 0;
@@ -312,7 +316,8 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
                     continue;
                 }
                 sk[loc] = kv[i];
-                if (HV) sv[loc] = vals[base + i * 32];
+                if constexpr (PF) sv[loc] = vv[i];
+                else if (HV) sv[loc] = vals[base + i * 32];
                 sb[loc] = (uint16_t)b;
             }
         }

@@ -582,11 +582,13 @@ k_seg_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restric
             const uint32_t base = lbase + w * (IT * 32) + lane;
             T kv[IT];
             uint32_t br[IT];   // bucket << 16 | rank inside the sub-tile's part of the bucket
+            uint32_t vv[HV ? IT : 1];   // payloads loaded with the keys (their latency overlaps the ranking)
 #pragma unroll
             for (int i = 0; i < IT; ++i) {
                 const uint32_t e = base + i * 32;
                 kv[i] = e < tend ? keys[r.beg + e] : T(0);
                 br[i] = e < tend ? (uint32_t)bid[r.beg + e] : (uint32_t)p;
+                if constexpr (HV) vv[i] = e < tend ? vals[r.beg + e] : 0u;
             }
             if (HV) {
                 for (int b = lane; b <= p; b += 32) mycnt[b] = 0;
@@ -640,7 +642,7 @@ k_seg_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restric
                             continue;
                         }
                         sk[loc] = kv[i];
-                        sv[loc] = vals[r.beg + base + i * 32];
+                        sv[loc] = vv[i];
                         sb[loc] = (uint16_t)b;
                     }
                 } else {
