@@ -401,7 +401,10 @@ struct LeafSmem {
     static constexpr size_t ex_bytes = (sizeof(E) * padded_len<E>(CAP) + 15) & ~size_t(15);
     // 4-byte keys alone: the per-warp key minima and maxima of the narrow test
     static constexpr bool NARROW = sizeof(O) == 4 && !HV;
-    static constexpr size_t red_bytes = NARROW ? sizeof(uint32_t) * 2 * (NT / 32) : 0;
+    // 8-byte keys with a payload: the same for the packed (offset, position) test
+    static constexpr bool PACK64 = sizeof(O) == 8 && HV;
+    static constexpr size_t red_bytes = NARROW ? sizeof(uint32_t) * 2 * (NT / 32)
+                                               : (PACK64 ? sizeof(uint64_t) * 2 * (NT / 32) : 0);
     static constexpr size_t bytes = ex_bytes + (HV ? sizeof(uint32_t) * CAP : 0) + red_bytes;
 };
 
@@ -452,6 +455,75 @@ __device__ __forceinline__ void leaf_sort(const typename KT::T* in, const uint32
             warp_register_sort<E, IT>(x, (int)len);
         }
         merge_rounds<E, NT, IT>(x, ex, (int)len, narrow ? 16 * IT : 32 * IT, narrow);
+    } else if constexpr (LS::PACK64) {
+        // 8-byte keys with a payload: (key, position) pairs, unique, whose key
+        // range spans less than 2^52 - 1 (the usual case: the keys of one leaf
+        // share their high bits) sort as single 64-bit words (key - kmin) << 12
+        // | position (positions < CAP = 4096), the same order as the pairs, on
+        // the 64-bit element path; other leaves sort the pairs.
+        static_assert(Cap<O>::v <= 4096, "positions fit 12 bits");
+        uint64_t* red = reinterpret_cast<uint64_t*>(smem + LS::ex_bytes + sizeof(uint32_t) * LS::CAP);
+        constexpr int LD = (LS::CAP + NT - 1) / NT;       // keys a thread loads
+        O kk[LD];
+        uint64_t kmin = ~0ull, kmax = 0;
+#pragma unroll
+        for (int i = 0; i < LD; ++i) {
+            const int j = threadIdx.x + i * NT;
+            kk[i] = j < (int)len ? KT::ord(in[beg + j]) : O(0);
+            if (j < (int)len) {
+                sv[j] = vin[beg + j];
+                kmin = min(kmin, (uint64_t)kk[i]);
+                kmax = max(kmax, (uint64_t)kk[i]);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+            kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            red[threadIdx.x >> 5] = kmin;
+            red[NT / 32 + (threadIdx.x >> 5)] = kmax;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ww = 0; ww < NT / 32; ++ww) {
+            kmin = min(kmin, red[ww]);
+            kmax = max(kmax, red[NT / 32 + ww]);
+        }
+        if (kmax - kmin < (1ull << 52) - 1) {
+            E64* ex64 = reinterpret_cast<E64*>(smem);
+#pragma unroll
+            for (int i = 0; i < LD; ++i) {
+                const int j = threadIdx.x + i * NT;
+                if (j < (int)len) ex64[pad_idx<E64>(j)] = E64{(((uint64_t)kk[i] - kmin) << 12) | (uint64_t)j};
+            }
+            __syncthreads();
+            E64 y[IT];
+#pragma unroll
+            for (int i = 0; i < IT; ++i) y[i] = base + i < (int)len ? ex64[pad_idx<E64>(base + i)] : EMax<E64>::v();
+            merge_sort_block<E64, NT, IT>(y, ex64, (int)len);
+#pragma unroll
+            for (int i = 0; i < IT; ++i)
+                if (base + i < (int)len) ex64[pad_idx<E64>(base + i)] = y[i];
+            __syncthreads();
+            for (int j = threadIdx.x; j < (int)len; j += NT) {
+                const uint64_t e = ex64[pad_idx<E64>(j)].k;
+                out[beg + j] = KT::key((O)(kmin + (e >> 12)));
+                vout[beg + j] = sv[(uint32_t)e & 0xFFFu];
+            }
+            __syncthreads();
+            return;
+        }
+#pragma unroll
+        for (int i = 0; i < LD; ++i) {
+            const int j = threadIdx.x + i * NT;
+            if (j < (int)len) ex[pad_idx<E>(j)] = LE::make(kk[i], (uint32_t)j);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < IT; ++i) x[i] = base + i < (int)len ? ex[pad_idx<E>(base + i)] : EMax<E>::v();
+        merge_sort_block<E, NT, IT>(x, ex, (int)len);
     } else {
         for (int j = threadIdx.x; j < (int)len; j += NT) {
             ex[pad_idx<E>(j)] = LE::make(KT::ord(in[beg + j]), (uint32_t)j);
