@@ -19,6 +19,8 @@
 #include "mergesort.cuh"
 #include "common.cuh"
 
+#include <type_traits>
+
 namespace ossort {
 
 // In-place exclusive scan of a[0, len) in shared memory by the whole block;
@@ -401,10 +403,10 @@ struct LeafSmem {
     static constexpr size_t ex_bytes = (sizeof(E) * padded_len<E>(CAP) + 15) & ~size_t(15);
     // 4-byte keys alone: the per-warp key minima and maxima of the narrow test
     static constexpr bool NARROW = sizeof(O) == 4 && !HV;
-    // 8-byte keys with a payload: the same for the packed (offset, position) test
-    static constexpr bool PACK64 = sizeof(O) == 8 && HV;
+    // keys with a payload: the same for the packed (offset, position) test
+    static constexpr bool PACK = HV;
     static constexpr size_t red_bytes = NARROW ? sizeof(uint32_t) * 2 * (NT / 32)
-                                               : (PACK64 ? sizeof(uint64_t) * 2 * (NT / 32) : 0);
+                                               : (PACK ? sizeof(uint64_t) * 2 * (NT / 32) : 0);
     static constexpr size_t bytes = ex_bytes + (HV ? sizeof(uint32_t) * CAP : 0) + red_bytes;
 };
 
@@ -455,13 +457,21 @@ __device__ __forceinline__ void leaf_sort(const typename KT::T* in, const uint32
             warp_register_sort<E, IT>(x, (int)len);
         }
         merge_rounds<E, NT, IT>(x, ex, (int)len, narrow ? 16 * IT : 32 * IT, narrow);
-    } else if constexpr (LS::PACK64) {
-        // 8-byte keys with a payload: (key, position) pairs, unique, whose key
-        // range spans less than 2^52 - 1 (the usual case: the keys of one leaf
-        // share their high bits) sort as single 64-bit words (key - kmin) << 12
-        // | position (positions < CAP = 4096), the same order as the pairs, on
-        // the 64-bit element path; other leaves sort the pairs.
-        static_assert(Cap<O>::v <= 4096, "positions fit 12 bits");
+    } else if constexpr (LS::PACK) {
+        // Keys with a payload: (key, position) pairs, unique.  In a leaf whose
+        // key range is narrow enough (the usual case: the keys of one leaf
+        // share their high bits) the pair packs into one word,
+        // (key - kmin) << PB | position, PB = log2(CAP) bits for positions,
+        // which orders as the pair does: 8-byte keys spanning less than
+        // 2^(64-PB) - 1 values sort 64-bit words instead of (key, position)
+        // triples, 4-byte keys spanning less than 2^(32-PB) - 1 sort 32-bit
+        // words on the register network instead of 64-bit pairs.  Other leaves
+        // sort the pairs.
+        using W = std::conditional_t<sizeof(O) == 8, uint64_t, uint32_t>;
+        using EP = std::conditional_t<sizeof(O) == 8, E64, E32>;
+        constexpr int PB = LS::CAP == 4096 ? 12 : 13;
+        static_assert((1 << PB) == LS::CAP, "positions fill PB bits");
+        constexpr W LIMIT = (W(1) << (8 * sizeof(W) - PB)) - 1;
         uint64_t* red = reinterpret_cast<uint64_t*>(smem + LS::ex_bytes + sizeof(uint32_t) * LS::CAP);
         constexpr int LD = (LS::CAP + NT - 1) / NT;       // keys a thread loads
         O kk[LD];
@@ -491,26 +501,27 @@ __device__ __forceinline__ void leaf_sort(const typename KT::T* in, const uint32
             kmin = min(kmin, red[ww]);
             kmax = max(kmax, red[NT / 32 + ww]);
         }
-        if (kmax - kmin < (1ull << 52) - 1) {
-            E64* ex64 = reinterpret_cast<E64*>(smem);
+        if (kmax - kmin < (uint64_t)LIMIT) {
+            EP* exp = reinterpret_cast<EP*>(smem);
+            const O omin = (O)kmin;
 #pragma unroll
             for (int i = 0; i < LD; ++i) {
                 const int j = threadIdx.x + i * NT;
-                if (j < (int)len) ex64[pad_idx<E64>(j)] = E64{(((uint64_t)kk[i] - kmin) << 12) | (uint64_t)j};
+                if (j < (int)len) exp[pad_idx<EP>(j)] = EP{(W)(((W)(kk[i] - omin) << PB) | (W)j)};
             }
             __syncthreads();
-            E64 y[IT];
+            EP y[IT];
 #pragma unroll
-            for (int i = 0; i < IT; ++i) y[i] = base + i < (int)len ? ex64[pad_idx<E64>(base + i)] : EMax<E64>::v();
-            merge_sort_block<E64, NT, IT>(y, ex64, (int)len);
+            for (int i = 0; i < IT; ++i) y[i] = base + i < (int)len ? exp[pad_idx<EP>(base + i)] : EMax<EP>::v();
+            merge_sort_block<EP, NT, IT>(y, exp, (int)len);
 #pragma unroll
             for (int i = 0; i < IT; ++i)
-                if (base + i < (int)len) ex64[pad_idx<E64>(base + i)] = y[i];
+                if (base + i < (int)len) exp[pad_idx<EP>(base + i)] = y[i];
             __syncthreads();
             for (int j = threadIdx.x; j < (int)len; j += NT) {
-                const uint64_t e = ex64[pad_idx<E64>(j)].k;
-                out[beg + j] = KT::key((O)(kmin + (e >> 12)));
-                vout[beg + j] = sv[(uint32_t)e & 0xFFFu];
+                const W e = exp[pad_idx<EP>(j)].k;
+                out[beg + j] = KT::key((O)(omin + (O)(e >> PB)));
+                vout[beg + j] = sv[(uint32_t)e & (uint32_t)(LS::CAP - 1)];
             }
             __syncthreads();
             return;
