@@ -413,7 +413,7 @@ void partition_top_cfg(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, 
                        const typename KT::O* spl_o, const uint32_t* spl_t, uint32_t p, typename KT::T* dst,
                        uint32_t* vdst, uint32_t* boff, uint32_t* bsize) {
     using SC = ScatterCfg<typename KT::T, HV, WIDE>;
-    const int lb = table_lbits(p);
+    const int lb = table_lbits_v(p);
     constexpr uint32_t SUPER = SC::SUPER;
     const uint32_t ntiles = (n + SUPER - 1) / SUPER;
     const uint32_t gmax = std::min<uint32_t>(std::max<uint32_t>(ntiles, 1), G_CAP);
@@ -422,20 +422,25 @@ void partition_top_cfg(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, 
     uint16_t* bid = c.ar.take<uint16_t>(n);
     if (!c.live()) return;
     constexpr int NTS = SC::NT;
-    auto kc = k_classify<KT, HV, WIDE>;
+    constexpr int NTC = 512;
+    // the vector classify over the same units (the payload takes no part in it)
+    auto kc = k_classify_v<KT, NTC, (int)SUPER>;
     auto ks = k_scatter<KT, HV, WIDE>;
     const size_t sm_c = classify_smem<KT>(p, lb), sm_s = scatter_smem<KT, HV, WIDE>(p);
     smem_at_least(reinterpret_cast<const void*>(kc), sm_c);
     smem_at_least(reinterpret_cast<const void*>(ks), sm_s);
     const int occ = occupancy(ks, NTS, sm_s);
     const uint32_t G = std::max<uint32_t>(1, std::min<uint32_t>(gmax, (uint32_t)(c.num_sms * occ)));
+    // cstep classify CTAs cover one scatter CTA's units (as in partition_top_v_cfg)
+    const uint32_t mc = std::max<uint32_t>(1, (uint32_t)(c.num_sms * occupancy(kc, NTC, sm_c)) / G);
+    const uint32_t cstep = (uint64_t)G * mc <= gmax ? mc : 1u;
     OS_LAUNCH(c.st, c.nested ? "k_classify.sample" : "k_classify",
-              kc<<<G, NTS, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, lb, hist, bid, ntiles));
+              kc<<<G * cstep, NTC, sm_c, c.st>>>(src, n, spl_o, spl_t, (int)p, lb, hist, bid, ntiles, nullptr));
     OS_LAUNCH(c.st, c.nested ? "k_column_scan.sample" : "k_column_scan",
-              k_column_scan<<<grid_for((uint64_t)p * 32, 256), 256, 0, c.st>>>(hist, p, G, col, bsize));
+              k_column_scan<<<grid_for((uint64_t)p * 32, 256), 256, 0, c.st>>>(hist, p, G * cstep, col, bsize));
     OS_LAUNCH(c.st, c.nested ? "k_bucket_offsets.sample" : "k_bucket_offsets", k_bucket_offsets<<<1, 1024, 0, c.st>>>(bsize, p, boff));
     OS_LAUNCH(c.st, c.nested ? "k_scatter.sample" : "k_scatter",
-              ks<<<G, NTS, sm_s, c.st>>>(src, vsrc, bid, n, (int)p, col, boff, dst, vdst, ntiles, c.status));
+              ks<<<G, NTS, sm_s, c.st>>>(src, vsrc, bid, n, (int)p, col, cstep, boff, dst, vdst, ntiles, c.status));
 }
 
 // Keys alone take the vector passes; payload sorts the stable pair above, with

@@ -122,59 +122,14 @@ __global__ void k_pick_splitters(const typename KT::T* __restrict__ tk, const ui
 }
 
 // ---------------------------------------------------------------------------
-// Step 4, pass 1: every CTA owns a contiguous run of units of SUPER keys
-// (the scatter's units, walked here in tiles of SUB), finds the bucket of each key
-// (tag = its position in the array), stores it in bid (two bytes a key, read
-// back by the scatter instead of searching again) and counts keys per bucket.
-// hist is bucket-major: hist[b * G + g].
+// Step 4: every CTA of the grid-wide passes owns a contiguous run of units of
+// SUPER keys: CTA g of G owns units [tile_lo(g, G), tile_lo(g + 1, G)).  Pass 1
+// (k_classify_v of distribute.cuh, with or without a payload) finds the bucket
+// of each key (tag = its position in the array), stores it in bid (two bytes a
+// key, read back by the scatter) and counts keys per bucket, bucket-major.
 // ---------------------------------------------------------------------------
 __host__ __device__ inline uint32_t tile_lo(uint32_t g, uint32_t G, uint32_t ntiles) {
     return (uint32_t)(((uint64_t)g * ntiles) / G);
-}
-
-template <class KT, bool HV, bool WIDE = false>
-__global__ void __launch_bounds__(ScatterCfg<typename KT::T, HV, WIDE>::NT,
-                                  ScatterCfg<typename KT::T, HV, WIDE>::NT >= 1024 ? 1
-                                  : (ScatterCfg<typename KT::T, HV, WIDE>::NT == 512 ? 2 : 3))
-k_classify(const typename KT::T* __restrict__ keys, uint32_t n, const typename KT::O* __restrict__ spl_o,
-           const uint32_t* __restrict__ spl_t, int p, int lbits, uint32_t* __restrict__ hist,
-           uint16_t* __restrict__ bid, uint32_t ntiles) {
-    using O = typename KT::O;
-    constexpr int NT = ScatterCfg<typename KT::T, HV, WIDE>::NT, SUPER = ScatterCfg<typename KT::T, HV, WIDE>::SUPER;
-    extern __shared__ __align__(16) char smem[];
-    SplitTable<O> tb;
-    tb.bind(smem, p - 1, lbits);
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + split_table_bytes<O>(p - 1, lbits));   // [p + 1]
-    for (int i = threadIdx.x; i < p - 1; i += NT) tb.set(i, spl_o[i], spl_t[i]);
-    for (int b = threadIdx.x; b <= p; b += NT) cnt[b] = 0;
-    __syncthreads();
-    split_table_finish<O>(tb, p - 1, lbits);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const uint32_t G = gridDim.x, g = blockIdx.x;
-    const uint32_t t0 = tile_lo(g, G, ntiles), t1 = tile_lo(g + 1, G, ntiles);
-    constexpr int SUB = NT * TOP_IT;
-    for (uint32_t th = t0 * (SUPER / SUB); th < t1 * (SUPER / SUB); ++th) {
-        const uint32_t base = th * SUB + w * (TOP_IT * 32) + lane;
-        O o[TOP_IT];
-#pragma unroll
-        for (int i = 0; i < TOP_IT; ++i) {
-            const uint32_t e = base + i * 32;
-            o[i] = e < n ? KT::ord(keys[e]) : O(0);
-        }
-#pragma unroll
-        for (int i = 0; i < TOP_IT; ++i) {
-            const uint32_t e = base + i * 32;
-            const bool valid = e < n;
-            int b = p;                       // past the end: a spare counter
-            if (valid) {
-                b = split_find<O>(tb, o[i], e);
-                bid[e] = (uint16_t)b;
-            }
-            warp_count((uint32_t)b, cnt);
-        }
-    }
-    __syncthreads();
-    for (int b = threadIdx.x; b < p; b += NT) hist[(size_t)b * G + g] = cnt[b];
 }
 
 // Exclusive scan of every bucket's column of CTA counts (one warp per bucket),
@@ -214,10 +169,10 @@ static __global__ void k_bucket_offsets(const uint32_t* __restrict__ bsize, uint
 }
 
 // ---------------------------------------------------------------------------
-// Step 4, pass 2: the same CTAs walk the same key ranges in tiles of SUB keys
-// (a whole unit for keys alone, so runs per bucket are as long as the unit
-// allows and fewer 32-byte sectors are partly written) and move the keys (and payloads) into their
-// buckets, using the bucket ids of pass 1.  Keys are
+// Step 4, pass 2 (payload sorts; keys alone take k_scatter_v): each scatter
+// CTA walks its units (those of cstep classify CTAs) in tiles of SUB keys and
+// moves the keys and payloads into their buckets, using the bucket ids of
+// pass 1 (a classify CTA count per bucket every cstep columns).  Keys are
 // staged in shared memory grouped by bucket and written out as contiguous runs.
 // With a payload the scatter is stable: a key's rank among the tile's keys of
 // its bucket comes from per-warp counters (peer masks from ballots) plus a
@@ -231,7 +186,7 @@ __global__ void __launch_bounds__(ScatterCfg<typename KT::T, HV, WIDE>::NT,
                                   : ScatterCfg<typename KT::T, HV, WIDE>::NT == 512 ? 2
                                   : (sizeof(typename KT::T) == 4 ? 4 : 3))
 k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ vals,
-          const uint16_t* __restrict__ bid, uint32_t n, int p, const uint32_t* __restrict__ col,
+          const uint16_t* __restrict__ bid, uint32_t n, int p, const uint32_t* __restrict__ col, uint32_t cstep,
           const uint32_t* __restrict__ boff, typename KT::T* __restrict__ out, uint32_t* __restrict__ vout,
           uint32_t ntiles, uint32_t* status) {
     using T = typename KT::T;
@@ -250,7 +205,9 @@ k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ 
     const int cstride = p + 1;
 
     const uint32_t G = gridDim.x, g = blockIdx.x;
-    for (int b = threadIdx.x; b < p; b += SNT) cursor[b] = boff[b] + col[(size_t)b * G + g];
+    // the classify ran with cstep CTAs per scatter CTA covering its units: this
+    // CTA's keys of bucket b start at column g * cstep
+    for (int b = threadIdx.x; b < p; b += SNT) cursor[b] = boff[b] + col[((size_t)b * G + g) * cstep];
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint16_t* mycnt = cnt + w * cstride;
