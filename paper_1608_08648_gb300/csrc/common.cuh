@@ -83,14 +83,15 @@ constexpr int TOP_WARPS = TOP_NT / 32;
 // stable-ranking counters must fit shared memory for p up to MAX_P) use 256
 // threads and 8192-key units in two halves.  Classify uses the same thread
 // count, since both passes split the array among the same number of CTAs.
-// WIDE (payload sorts of 4-byte keys with p <= HV_WIDE_MAX_P, where the
-// counters of 32 warps still fit): 1024 threads and 16384-key tiles, so that
-// each bucket's run in a tile spans whole 32-byte sectors more often, and the
-// payloads are loaded with the keys instead of after the ranking (measured on
-// GB300, int32 + payload at p = 512: 3.69 -> 3.00 ms).
-constexpr int HV_WIDE_MAX_P = 768;
+// WIDE (payload sorts with p <= hv_wide_max_p, where the per-warp counters
+// still fit): 4-byte keys 1024 threads and 16384-key tiles, 8-byte keys 768
+// threads and 12288-key tiles, so that each bucket's run in a tile spans whole
+// 32-byte sectors more often, and the payloads are loaded with the keys instead
+// of after the ranking (measured on GB300, int32 + payload at p = 512: 3.69 ->
+// 3.00 ms).
+template <class T> constexpr int hv_wide_max_p() { return sizeof(T) == 4 ? 768 : 1024; }
 template <class T, bool HV, bool WIDE = false> struct ScatterCfg {
-    static constexpr int NT = WIDE ? 4 * TOP_NT : (HV ? TOP_NT : 2 * TOP_NT);
+    static constexpr int NT = WIDE ? (sizeof(T) == 4 ? 4 * TOP_NT : 3 * TOP_NT) : (HV ? TOP_NT : 2 * TOP_NT);
     static constexpr int WARPS = NT / 32;
     static constexpr int SUB = NT * TOP_IT;
     static constexpr int SUPER = SUB > 2 * TOP_TILE ? SUB : 2 * TOP_TILE;

@@ -444,21 +444,19 @@ void partition_top_cfg(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, 
 }
 
 // Keys alone take the vector passes; payload sorts the stable pair above, with
-// the WIDE configuration for 4-byte keys while p <= HV_WIDE_MAX_P (a choice on
-// p alone, so that the workspace plan and the launches agree).
+// the WIDE configuration while p <= hv_wide_max_p (a choice on p alone, so that
+// the workspace plan and the launches agree).
 template <class KT, bool HV>
 void partition_top(Ctx& c, const typename KT::T* src, const uint32_t* vsrc, uint32_t n,
                    const typename KT::O* spl_o, const uint32_t* spl_t, uint32_t p, typename KT::T* dst,
                    uint32_t* vdst, uint32_t* boff, uint32_t* bsize) {
     if constexpr (!HV) {
         partition_top_v<KT>(c, src, n, spl_o, spl_t, p, dst, boff, bsize);
-    } else if constexpr (sizeof(typename KT::T) == 4) {
-        if (p <= (uint32_t)HV_WIDE_MAX_P)
+    } else {
+        if (p <= (uint32_t)hv_wide_max_p<typename KT::T>())
             partition_top_cfg<KT, HV, true>(c, src, vsrc, n, spl_o, spl_t, p, dst, vdst, boff, bsize);
         else
             partition_top_cfg<KT, HV, false>(c, src, vsrc, n, spl_o, spl_t, p, dst, vdst, boff, bsize);
-    } else {
-        partition_top_cfg<KT, HV, false>(c, src, vsrc, n, spl_o, spl_t, p, dst, vdst, boff, bsize);
     }
 }
 

@@ -182,7 +182,7 @@ static __global__ void k_bucket_offsets(const uint32_t* __restrict__ bsize, uint
 // ---------------------------------------------------------------------------
 template <class KT, bool HV, bool WIDE = false>
 __global__ void __launch_bounds__(ScatterCfg<typename KT::T, HV, WIDE>::NT,
-                                  ScatterCfg<typename KT::T, HV, WIDE>::NT >= 1024 ? 1
+                                  ScatterCfg<typename KT::T, HV, WIDE>::NT >= 768 ? 1
                                   : ScatterCfg<typename KT::T, HV, WIDE>::NT == 512 ? 2
                                   : (sizeof(typename KT::T) == 4 ? 4 : 3))
 k_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restrict__ vals,
