@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--s", type=int, default=16)
     ap.add_argument("--p-f64", type=int, default=1024, help="p of the float64 sub-record of the int32 line")
     ap.add_argument("--no-f64", action="store_true", help="leave the float64 sub-record out of the int32 line")
+    ap.add_argument("--p-kv", type=int, default=1024, help="p of the stable key-value sub-record of the int32 line")
+    ap.add_argument("--no-kv", action="store_true", help="leave the stable key-value sub-record out of the int32 line")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--det-merge", action="store_true",
                     help="SqDet with steps 4-5 as in Algorithm 1 (split the sorted sequences, merge every bucket)")
@@ -209,7 +211,8 @@ def measured_pipe(kernel: str, dtype: str):
                 f"{t.get('n_captured')} keys)")
 
 
-def algorithmic_bytes(name: str, n: int, kb: int, vb: int, repart_keys: int, split_keys: int = 0) -> int:
+def algorithmic_bytes(name: str, n: int, kb: int, vb: int, repart_keys: int, split_keys: int = 0,
+                      p: int = 0) -> int:
     """Bytes a kernel must move for one step (one full sort of n keys), the minimum
     ledger of one distribution level (no stored bucket ids): classify reads every key;
     scatter reads and writes every key (and payload); the bucket phase's split does
@@ -228,6 +231,10 @@ def algorithmic_bytes(name: str, n: int, kb: int, vb: int, repart_keys: int, spl
     if name == "k_repart":
         rk = repart_keys - split_keys
         return rk * (2 * kb + vb) + rk * (kb + vb)
+    if name == "k_det_gather":            # split + merge SqDet: every piece copied into its bucket once
+        return 2 * n * (kb + vb)
+    if name == "k_det_merge":             # ceil(log2 p) pairwise passes, each reading and writing every key
+        return 2 * n * (kb + vb) * max(1, (max(p, 2) - 1).bit_length())
     return 0
 
 
@@ -254,8 +261,8 @@ def pipeline_ledger(n, kb, vb, split_keys, repart_keys, ms, peak, dtype=None, p=
     return {"actual_bytes": actual, "actual_gbs": round(actual / t / 1e9, 1), "actual_frac": round(actual / t / 1e9 / peak, 4),
             "min_bytes": minimum, "min_gbs": round(minimum / t / 1e9, 1), "min_frac": round(minimum / t / 1e9 / peak, 4),
             "ncu_dram_bytes": ncu,
-            "ncu_note": "DRAM read + write of the five passes from the committed ncu capture at 2^25 keys, "
-                        "scaled per key (part of that capture's traffic stays in the 129 MB L2)",
+            "ncu_note": "DRAM read + write of the five passes from the committed one-launch ncu captures at 2^27 keys, "
+                        "scaled per key (2^27 keys fill the 129 MB L2 four times over)",
             "comparisons": round(comps), "gcomparisons_per_s": round(comps / t / 1e9, 1),
             "passes": "classify, scatter, bucket-phase split (classify + scatter), repartition, leaf sort"}
 
@@ -808,11 +815,14 @@ def host_link_gbs(h_buf, d_buf, stream, reps=3):
     return res
 
 
-def time_sort(a, dtype, p, rank, world, local, steps, warmup, with_e2e=True):
+def time_sort(a, dtype, p, rank, world, local, steps, warmup, with_e2e=True, kv=False):
     """One key type's sort of the configured n: the timed region (profiler off),
     a second pass of the same steps with the library's per-launch event profiler
     on (per-kernel device times, dominant kernel, roofline), the statistics of one
-    untimed sort, and the end-to-end variant through host buffers."""
+    untimed sort, and the end-to-end variant through host buffers.  kv: the stable
+    key-value workload instead (u64 keys, a quarter of them copies of 1,000 hot
+    values, with the original index as a 4-byte payload; checked against a stable
+    torch sort)."""
     import torch
 
     import paper_1608_08648_gb300 as oss
@@ -821,18 +831,27 @@ def time_sort(a, dtype, p, rank, world, local, steps, warmup, with_e2e=True):
     dev = torch.device("cuda", local)
     n = a.keys
     kt = oss.KEY_TYPES[dtype]
-    kb, vb = KEY_BYTES[dtype], 0
-    keys = inputs.keys(a.dist, n, dtype, seed=a.seed + rank, p=p, device=dev)
+    kb, vb = KEY_BYTES[dtype], (4 if kv else 0)
+    if kv:
+        assert dtype == "u64"
+        keys = inputs.hot_u64_keys(n, seed=2 + rank, device=dev)
+        vals = torch.arange(n, dtype=torch.int32, device=dev)
+        vout = torch.empty_like(vals)
+    else:
+        keys = inputs.keys(a.dist, n, dtype, seed=a.seed + rank, p=p, device=dev)
+        vals = vout = None
     out = torch.empty_like(keys)
     prm = oss.params(a.split, p, a.s, a.seed, oss.OS_STABLE | (2 if a.det_merge else 0))
-    rc, need = oss.os_workspace_size(kt, n, False, prm)
+    rc, need = oss.os_workspace_size(kt, n, kv, prm)
     assert rc == 0, oss.os_strerror(rc)
     ws = torch.empty(need, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     sh = stream.cuda_stream
+    vin_p = vals.data_ptr() if kv else None
+    vout_p = vout.data_ptr() if kv else None
 
     def step():
-        r = oss.os_sort(kt, keys.data_ptr(), out.data_ptr(), None, None, n, prm, ws.data_ptr(), need, sh, None)
+        r = oss.os_sort(kt, keys.data_ptr(), out.data_ptr(), vin_p, vout_p, n, prm, ws.data_ptr(), need, sh, None)
         if r != 0:
             raise RuntimeError(f"os_sort failed: {oss.os_strerror(r)} (cuda {oss.os_last_cuda_error()})")
 
@@ -842,7 +861,13 @@ def time_sort(a, dtype, p, rank, world, local, steps, warmup, with_e2e=True):
     assert rc == 0 and bits == 0, f"device status {bits:#x}"
     # correctness of the last warm-up output (not timed): ordered and a permutation
     ok = out.view(torch.int64) if dtype == "u64" else out
-    if dtype == "f64":
+    if kv:
+        # stable: keys in unsigned order, equal keys in input order (payload = original index)
+        perm = torch.sort(keys.view(torch.int64) ^ torch.iinfo(torch.int64).min, stable=True).indices
+        assert torch.equal(out, keys[perm]), "key-value output not ordered"
+        assert torch.equal(vout.to(torch.int64), perm), "payloads not in stable order"
+        del perm
+    elif dtype == "f64":
         b = out.view(torch.int64)
         ordk = torch.where(b < 0, b ^ torch.iinfo(torch.int64).max, b)   # signed-comparable totalOrder
         assert bool((ordk[1:] >= ordk[:-1]).all()), "output not ordered"
@@ -852,8 +877,8 @@ def time_sort(a, dtype, p, rank, world, local, steps, warmup, with_e2e=True):
     assert torch.equal(torch.sort(keys.view(torch.int64) if dtype != "i32" else keys).values,
                        torch.sort(out.view(torch.int64) if dtype != "i32" else out).values), "not a permutation"
     # statistics of one untimed sort: repartitioned keys (for the byte ledger)
-    _, _, st = oss.sort(keys, split=a.split, p=p, s=a.s, seed=a.seed, out=out, workspace=ws, key_type=dtype,
-                        stats=True, det_merge=a.det_merge)
+    _, _, st = oss.sort(keys, vals, split=a.split, p=p, s=a.s, seed=a.seed, out=out, values_out=vout, workspace=ws,
+                        key_type=dtype, stats=True, det_merge=a.det_merge)
     torch.cuda.synchronize()
     _, ctr = oss.os_read_counters(ws.data_ptr(), sh)
     split_keys = ctr["split_keys"]
@@ -950,7 +975,7 @@ def time_sort(a, dtype, p, rank, world, local, steps, warmup, with_e2e=True):
     t1e.record(stream)
     torch.cuda.synchronize()
     torch_sort_ms = t0e.elapsed_time(t1e) / 3
-    del tk, keys, out
+    del tk, keys, out, vals, vout
     torch.cuda.empty_cache()
 
     # roofline of the dominant kernel (top-level launches only), from the profiled pass
@@ -959,7 +984,7 @@ def time_sort(a, dtype, p, rank, world, local, steps, warmup, with_e2e=True):
     dom = max(top, key=lambda k: k["total_ms"]) if top else None
     roof = None
     if dom:
-        alg = algorithmic_bytes(dom["name"], n, kb, vb, st["repart_keys"], split_keys) * steps
+        alg = algorithmic_bytes(dom["name"], n, kb, vb, st["repart_keys"], split_keys, p) * steps
         achieved = alg / (dom["total_ms"] / 1e3) / 1e9 if dom["total_ms"] > 0 else 0.0
         peak = float(peaks["hbm_gbs"])
         roof = {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1), "peak": peak,
@@ -967,7 +992,7 @@ def time_sort(a, dtype, p, rank, world, local, steps, warmup, with_e2e=True):
                 "traffic": measured_traffic(dom["name"], dtype, n),
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "avg_launch_ms": round(dom["total_ms"] / dom["launches"], 4),
-                "alg_bytes_per_step": algorithmic_bytes(dom["name"], n, kb, vb, st["repart_keys"], split_keys),
+                "alg_bytes_per_step": algorithmic_bytes(dom["name"], n, kb, vb, st["repart_keys"], split_keys, p),
                 "timing": "CUDA events around every launch of the kernel on its stream, in a second pass of the "
                           "same steps with the library's event profiler on",
                 "secondary": measured_pipe(dom["name"], dtype),
@@ -1021,6 +1046,20 @@ def run_ours(a, rank, world, local):
         if rank == 0 and world == 1 and not a.no_cpu:
             sub["cpu_baseline"] = cpu_baseline(a, "f64", pf, sample=min(a.cpu_sample, 1 << 22), runs=1)
         res["f64"] = sub
+    # the stable key-value workload: u64 keys with hot values and a 4-byte payload
+    if a.dtype == "i32" and not a.no_kv:
+        torch.cuda.empty_cache()
+        pk = a.p_kv
+        rk = time_sort(a, "u64", pk, rank, world, local, a.steps, a.warmup, with_e2e=False, kv=True)
+        nn = '2^%d' % (n.bit_length() - 1) if n & (n - 1) == 0 else str(n)
+        sub = {"workload": f"n={n} ({nn}) pairs: u64 key (uniform, a quarter of the positions copying one of "
+                           f"1,000 hot values, seed 2) + u32 original index, stable "
+                           f"Sq{'Ran' if a.split == 'ran' else 'Det'} p={pk} s={a.s}",
+               "value": rk["value"], "unit": "keys/s", "ms_per_step": rk["ms"], "dtype": "u64+u32", "p": pk,
+               "s": a.s, "stable": True, "roofline": rk["roofline"], "gpu_launches": rk["launches"],
+               "clocks": rk["clocks"]}
+        sub.update(sort_summary(a, rk))
+        res["kv"] = sub
     if not a.no_batched:
         torch.cuda.empty_cache()
         bt = run_batched(a, rank, world, local, steps=max(3, min(a.steps, 10)), warmup=3,
