@@ -623,11 +623,14 @@ k_seg_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restric
 #pragma unroll
                 for (int i = 0; i < IT; ++i) {
                     const uint32_t b = br[i];
-                    br[i] = (b << 16) | warp_slot(b, tile_off);
+                    br[i] = (b << 16) | atomicAdd(&tile_off[b], 1u);
                 }
             }
             const uint32_t tvalid = block_exclusive_scan(tile_off, p, scratch);
             if (threadIdx.x == 0) tile_off[p] = tvalid;
+            // cursor[b] becomes the offset of staged index j's destination: dst =
+            // cursor[b] + j (restored below, by the thread that owns b)
+            for (int b = threadIdx.x; b < p; b += SNT) cursor[b] -= tile_off[b];
             // range checks predicate the accesses; a failed one is reported once
             // per thread after the write-out (no branch per key)
             uint32_t bad_site = 0, bad_at = 0;
@@ -659,7 +662,7 @@ k_seg_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restric
             for (uint32_t j = threadIdx.x; j < tvalid; j += SNT) {
                 const int b = sb[j];                       // >= p: a slot no key was staged to
                 const int bc = min(b, p - 1);              // cursor holds p entries
-                const uint32_t dst = cursor[bc] + (j - tile_off[bc]);
+                const uint32_t dst = cursor[bc] + j;
                 const bool ok = b < p && dst >= r.beg && dst < seg_end;
                 if (ok) {
                     out[dst] = sk[j];
@@ -669,7 +672,7 @@ k_seg_scatter(const typename KT::T* __restrict__ keys, const uint32_t* __restric
             }
             if (bad_site) flag_bounds(status, bad_site, bad_at);
             __syncthreads();
-            for (int b = threadIdx.x; b < p; b += SNT) cursor[b] += tile_off[b + 1] - tile_off[b];
+            for (int b = threadIdx.x; b < p; b += SNT) cursor[b] += tile_off[b + 1];
             __syncthreads();
         }
     }
