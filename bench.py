@@ -55,10 +55,11 @@ def parse():
     ap.add_argument("--ref-sample", type=int, default=1 << 20, help="keys per step of --impl reference")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="sort", choices=["sort", "batched", "serving", "strings"],
+    ap.add_argument("--workload", default="sort", choices=["sort", "batched", "serving", "strings", "sweep"],
                     help="sort: one array (the headline line, with 'batched' and 'serving' summaries); batched / "
                          "serving / strings (the paper's 32-byte keys, Table 1 grid): that workload as the "
-                         "line's own metric")
+                         "line's own metric; sweep: the single-array sweep at 2^27 keys (int32 and float64, "
+                         "SqDet and SqRan, seven distributions), one table")
     ap.add_argument("--no-batched", action="store_true", help="leave the batched summary out of the sort line")
     ap.add_argument("--no-serving", action="store_true", help="leave the serving summary out of the sort line")
     ap.add_argument("--requests", type=int, default=20000, help="serving: requests of the replayed trace")
@@ -1168,6 +1169,91 @@ def cpu_baseline(a, dtype, p, sample=None, runs=3):
                                 "seconds": round(t_ss, 3)}}
 
 
+# ---- the single-array sweep ---------------------------------------------------------
+
+SWEEP = {"n": 1 << 27, "p": 1024, "s": 16, "seed": 1}
+
+
+def run_sweep_line(a, rank, world, local):
+    """The single-array sweep: n = 2^27 keys, int32 and float64, SqRan and SqDet with
+    p = 1024, s (r) = 16, every distribution of inputs.DISTRIBUTIONS from seed 1.  Each
+    cell: W untimed sorts, then K sorts timed with CUDA events on the launching stream
+    (inputs of 512 MiB / 1 GiB, above L2); the output of a warm-up sort is checked to be
+    ordered and a permutation of the input.  The line's value is the geometric mean of
+    the cells' keys/s; the table holds every cell."""
+    import math
+
+    import torch
+
+    import paper_1608_08648_gb300 as oss
+    from paper_1608_08648_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, p, s_, seed = SWEEP["n"], SWEEP["p"], SWEEP["s"], SWEEP["seed"]
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    rows = []
+    launches0 = oss.os_launch_count()
+    clocks = Clocks(local)
+    clocks.start()
+    for dtype in ("i32", "f64"):
+        kt = oss.KEY_TYPES[dtype]
+        for split in ("ran", "det"):
+            prm = oss.params(split, p, s_, seed, oss.OS_STABLE)
+            rc, need = oss.os_workspace_size(kt, n, False, prm)
+            assert rc == 0, oss.os_strerror(rc)
+            ws = torch.empty(need, dtype=torch.uint8, device=dev)
+            for dist in inputs.DISTRIBUTIONS:
+                keys = inputs.keys(dist, n, dtype, seed=seed + rank, p=p, device=dev)
+                out = torch.empty_like(keys)
+
+                def step():
+                    r = oss.os_sort(kt, keys.data_ptr(), out.data_ptr(), None, None, n, prm, ws.data_ptr(), need,
+                                    sh, None)
+                    if r != 0:
+                        raise RuntimeError(f"os_sort failed: {oss.os_strerror(r)}")
+
+                for _ in range(a.warmup):
+                    step()
+                rc, bits = oss.os_check(ws.data_ptr(), sh)
+                assert rc == 0 and bits == 0, f"device status {bits:#x}"
+                if dtype == "f64":
+                    b = out.view(torch.int64)
+                    ok = torch.where(b < 0, b ^ torch.iinfo(torch.int64).max, b)
+                    kb = keys.view(torch.int64)
+                    ref = torch.sort(torch.where(kb < 0, kb ^ torch.iinfo(torch.int64).max, kb)).values
+                else:
+                    ok = out
+                    ref = torch.sort(keys).values
+                assert torch.equal(ok, ref), f"{dtype} {split} {dist}: output differs from a sort of the input"
+                del ok, ref
+                barrier(world)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(a.steps):
+                    step()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = max_over_ranks(e0.elapsed_time(e1) / a.steps, world)
+                rows.append({"dtype": dtype, "split": split, "dist": dist, "ms": round(ms, 3),
+                             "keys_per_s": world * n / (ms / 1e3)})
+                del keys, out
+            del ws
+            torch.cuda.empty_cache()
+    clk = clocks.stop()
+    geo = math.exp(sum(math.log(r["keys_per_s"]) for r in rows) / len(rows))
+    return {"metric": "keys/s (single-array sweep, geometric mean of the cells)", "value": geo, "unit": "keys/s",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": round(sum(r["ms"] for r in rows) / len(rows), 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "i32+f64", "data": "synthetic",
+            "config": {"workload": f"n={n} (2^27) int32 and float64 keys, SqRan and SqDet p={p} s={s_}, "
+                                   f"distributions {', '.join(inputs.DISTRIBUTIONS)}, seed {seed}",
+                       "l2": "inputs larger than L2 (no flush needed)", "parallelism": "replicas"},
+            "table": rows, "gpu_launches": oss.os_launch_count() - launches0, "clocks": clk}
+
+
 # ---- reference arm: the CPU oracle ------------------------------------------------
 
 def run_reference(a, rank, world):
@@ -1287,6 +1373,8 @@ def main():
             res = run_serving_line(a, rank, world, local)
         elif a.workload == "strings":
             res = run_strings_line(a, rank, world, local)
+        elif a.workload == "sweep":
+            res = run_sweep_line(a, rank, world, local)
         else:
             res = run_ours(a, rank, world, local)
     if rank == 0 and res is not None:
