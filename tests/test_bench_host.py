@@ -33,9 +33,24 @@ def test_traffic_used_only_for_its_sources(tmp_path, monkeypatch):
     per = t["dram_bytes_per_key"]["k_leaf"]
     monkeypatch.setattr(bench, "cuda_source_sha", lambda: t["source_sha"])
     assert bench.measured_traffic("k_leaf", "i32", 1000) == int(per * 1000)
+    with open(os.path.join(bench.ROOT, "profiles", "kernel_traffic_f64.json")) as f:
+        t64 = json.load(f)
+    monkeypatch.setattr(bench, "cuda_source_sha", lambda: t64["source_sha"])
+    assert bench.measured_traffic("k_leaf", "f64", 1000) == int(t64["dram_bytes_per_key"]["k_leaf"] * 1000)
     monkeypatch.setattr(bench, "cuda_source_sha", lambda: "0" * 16)
     assert bench.measured_traffic("k_leaf", "i32", 1000) is None
-    assert bench.measured_traffic("k_leaf", "f64", 1000) is None      # no capture for float64
+    assert bench.measured_traffic("k_leaf", "f64", 1000) is None
+    assert bench.measured_traffic("k_leaf", "u64", 1000) is None      # no capture for uint64
+
+
+def test_split_merge_ledger():
+    """The split + merge SqDet: one gather pass, then ceil(log2 p) pairwise merge passes,
+    each reading and writing every key and payload."""
+    n = 1 << 20
+    assert bench.algorithmic_bytes("k_det_gather", n, 4, 0, 0) == 8 * n
+    assert bench.algorithmic_bytes("k_det_merge", n, 4, 0, 0, 0, 1024) == 8 * n * 10
+    assert bench.algorithmic_bytes("k_det_merge", n, 8, 4, 0, 0, 1000) == 24 * n * 10
+    assert bench.algorithmic_bytes("k_det_merge", n, 4, 0, 0, 0, 2) == 8 * n
 
 
 def test_secondary_bound_used_only_for_its_sources(monkeypatch):
